@@ -1,0 +1,152 @@
+/*
+ * leg.h -- C ABI of the GB300 (sm_103a) Legendre-coefficient library.
+ *
+ * Method: De Micheli & Viano, "A new and efficient method for the computation
+ * of Legendre coefficients" (arXiv:1106.0463).  For f(x) = sum_n c_n P_n(x)
+ * (Eq. 2.1) with c_n = (n + 1/2) int_{-1}^{1} f P_n dx (Eq. 2.3), Theorem 1
+ * (Eq. 2.4, Eq. 2.5) gives a_n = c_n / (2n+1) as the nonnegative-index Fourier
+ * coefficients of the Abel-type transform
+ *     fhat(y) = eps(y) e^{iy/2} / (2 pi i) * int_{cos y}^{1} f(x) / sqrt(2(x - cos y)) dx.
+ * The library evaluates fhat on the periodic grid y_j = 2 pi j / M by
+ * quadrature (substitution x = cos y + s^2, Gauss-Legendre in s; Sec. 2, the
+ * paragraph after Eq. 2.14) and takes one length-M FFT (the paragraph that
+ * follows it).  For f given by samples at the K Chebyshev-Lobatto nodes the
+ * Abel step is a dense (M/2+1) x K operator applied to a batch of functions
+ * (the rows j and M-j coincide by the symmetry Eq. 2.12).
+ *
+ * Conventions used by every entry point:
+ *  - Input samples: f[b*K + k] = f_b(x_k), x_k = cos(pi k / (K-1)),
+ *    k = 0..K-1 (x_0 = +1 first, x_{K-1} = -1 last), row-major B x K.
+ *  - Output: c[b*N + n] = c_n of function b, n = 0..N-1, row-major B x N.
+ *  - All array pointers are DEVICE pointers unless stated otherwise; the
+ *    caller owns them.  Nothing is copied to or from the host, and no call
+ *    synchronises the host with the stream (except leg_plan_create and the
+ *    first call that grows a plan's workspace, see leg_plan_reserve).
+ *  - Calls are asynchronous on the given stream (0 = legacy default stream).
+ *  - Return value: LEG_OK (0) or one of the LEG_ERR_* codes below; a
+ *    human-readable message for the last error of the calling thread is
+ *    returned by leg_last_error().  Argument errors are reported before any
+ *    work is enqueued.
+ */
+#ifndef LEG_H
+#define LEG_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define LEG_OK               0
+#define LEG_ERR_INVALID_ARG  1  /* bad size, null pointer, bad enum, N > M/2 ... */
+#define LEG_ERR_OOM          2  /* device or host allocation failed            */
+#define LEG_ERR_CUDA         3  /* a CUDA runtime/driver call failed           */
+#define LEG_ERR_UNSUPPORTED  4  /* valid request this build does not implement */
+#define LEG_ERR_TIMEOUT      5  /* a bounded device-side wait expired          */
+
+/* ---- arithmetic of a plan ---------------------------------------------- */
+/*
+ * The operator itself is always built in FP64 (Gauss nodes and weights, the
+ * node mapping 1 - x = 2 sin^2(y/2)(1 - tau^2), barycentric interpolation).
+ * The dtype selects how it is applied:
+ *   LEG_F64        f, c in FP64; FP64 GEMM on the CUDA cores, FP64 FFT.
+ *                  The plain FP64 GPU path.
+ *   LEG_F32        f, c in FP32; FP32 GEMM on the CUDA cores (FFMA), FP32 FFT.
+ *   LEG_BF16       f, c in FP32; one BF16 x BF16 tensor-core product with
+ *                  FP32 accumulation (tcgen05), FP32 FFT.
+ *   LEG_SPLIT_FP16 f, c in FP32; operator and input each split into three
+ *                  FP16 slices (a fixed-point leading slice, two residual
+ *                  slices), six tcgen05 products into three FP32 TMEM
+ *                  accumulators of which the leading one is exact, combined
+ *                  into a double-float result; double-float FFT.  The path
+ *                  that meets a 1e-6 relative error.
+ */
+typedef enum {
+    LEG_F64 = 0,
+    LEG_F32 = 1,
+    LEG_BF16 = 2,
+    LEG_SPLIT_FP16 = 3
+} leg_dtype;
+
+/* plan flags (leg_plan_create_ex) */
+#define LEG_FLAG_TAU_LITERAL 1u  /* Q-point Gauss rule mapped onto tau in [0,1]
+                                    instead of the nonnegative half of a
+                                    2Q-point rule (the default)               */
+
+typedef struct leg_plan *leg_plan_t;
+
+/*
+ * leg_plan_create -- build the Abel-interpolation operator for one problem size.
+ *   N  number of coefficients returned, 1 <= N <= M/2.
+ *   M  trapezoid points on [0, 2 pi), a power of two, 8 <= M <= 32768.
+ *   K  Chebyshev-Lobatto samples per function, 2 <= K <= 16385.
+ *   Q  distinct Gauss nodes per y-point in the Abel integral; Q = 0 selects
+ *      ceil(K/2), which integrates the degree-(K-1) interpolant exactly.
+ *   dtype  one of leg_dtype.
+ * Builds the operator on the current device (FP64 kernels), derives the
+ * operand planes for dtype, and stores them in device memory owned by the
+ * plan.  Synchronises the host with the device once.  *out receives the
+ * plan; on error *out is set to NULL.
+ * Errors: LEG_ERR_INVALID_ARG (sizes, dtype, out == NULL), LEG_ERR_OOM,
+ * LEG_ERR_CUDA, LEG_ERR_UNSUPPORTED (dtype not available for this size).
+ */
+int leg_plan_create(leg_plan_t *out, int N, int M, int K, int Q, int dtype);
+int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, int dtype, unsigned flags);
+
+/* Releases every device buffer of the plan.  NULL is accepted. */
+int leg_plan_destroy(leg_plan_t plan);
+
+/*
+ * leg_plan_reserve -- make the plan's workspace large enough for batches of
+ * up to B functions.  Allocation synchronises; call it before capturing
+ * leg_forward / leg_backward into a CUDA graph.  leg_forward grows the
+ * workspace by itself when B exceeds the reservation.
+ */
+int leg_plan_reserve(leg_plan_t plan, int B);
+
+/* Sizes of a plan: N, M, K, Q (resolved), dtype, padded K, rows M/2+1. */
+int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *dtype,
+                  int *K_padded, int *rows);
+
+/*
+ * leg_forward -- c = L f for a batch of B functions (Theorem 1, Eq. 2.4-2.5).
+ *   f  device, B x K row-major (FP64 for LEG_F64, FP32 otherwise).
+ *   c  device, B x N row-major (FP64 for LEG_F64, FP32 otherwise).
+ *   B  >= 0; B = 0 is a no-op.
+ * Enqueued on stream; f and c must not overlap.  Concurrent calls on one
+ * plan from different streams race on its workspace: use one plan per stream.
+ */
+int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream);
+
+/*
+ * leg_backward -- df = L^T dc, the exact adjoint (transpose) of the linear
+ * map of leg_forward for the same plan: the transposed twist + Fourier sum
+ * followed by the transposed Abel operator.
+ *   dc device, B x N (FP64 for LEG_F64, FP32 otherwise).
+ *   df device, B x K (same type); overwritten.
+ */
+int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaStream_t stream);
+
+/*
+ * leg_plain_forward -- the plain method: the Abel integral of a closed-form
+ * function evaluated at the quadrature points themselves (no interpolation),
+ * then the same FFT.  FP64 throughout; uses N, M, Q of the plan (any dtype).
+ *   family  LEG_FAMILY_GENFN: f(x) = (1 - 2 x t + t^2)^(-1/2)  (Eq. 2.2),
+ *                            params[b] = t, |t| < 1;
+ *           LEG_FAMILY_EXP:   f(x) = exp(a x), params[b] = a.
+ *   params  device, B doubles.   c  device, B x N doubles.
+ */
+#define LEG_FAMILY_GENFN 0
+#define LEG_FAMILY_EXP   1
+int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
+                      double *c, cudaStream_t stream);
+
+/* Message for the most recent failing call on this host thread ("" if none). */
+const char *leg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LEG_H */
