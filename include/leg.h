@@ -34,6 +34,12 @@
 #include <stddef.h>
 #include <cuda_runtime_api.h>
 
+#if defined(__GNUC__)
+#define LEG_API __attribute__((visibility("default")))
+#else
+#define LEG_API
+#endif
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -92,11 +98,11 @@ typedef struct leg_plan *leg_plan_t;
  * Errors: LEG_ERR_INVALID_ARG (sizes, dtype, out == NULL), LEG_ERR_OOM,
  * LEG_ERR_CUDA, LEG_ERR_UNSUPPORTED (dtype not available for this size).
  */
-int leg_plan_create(leg_plan_t *out, int N, int M, int K, int Q, int dtype);
-int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, int dtype, unsigned flags);
+LEG_API int leg_plan_create(leg_plan_t *out, int N, int M, int K, int Q, int dtype);
+LEG_API int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, int dtype, unsigned flags);
 
 /* Releases every device buffer of the plan.  NULL is accepted. */
-int leg_plan_destroy(leg_plan_t plan);
+LEG_API int leg_plan_destroy(leg_plan_t plan);
 
 /*
  * leg_plan_reserve -- make the plan's workspace large enough for batches of
@@ -104,10 +110,10 @@ int leg_plan_destroy(leg_plan_t plan);
  * leg_forward / leg_backward into a CUDA graph.  leg_forward grows the
  * workspace by itself when B exceeds the reservation.
  */
-int leg_plan_reserve(leg_plan_t plan, int B);
+LEG_API int leg_plan_reserve(leg_plan_t plan, int B);
 
 /* Sizes of a plan: N, M, K, Q (resolved), dtype, padded K, rows M/2+1. */
-int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *dtype,
+LEG_API int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *dtype,
                   int *K_padded, int *rows);
 
 /*
@@ -118,7 +124,17 @@ int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *dtype,
  * Enqueued on stream; f and c must not overlap.  Concurrent calls on one
  * plan from different streams race on its workspace: use one plan per stream.
  */
-int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream);
+LEG_API int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream);
+
+/*
+ * leg_forward_profiled -- leg_forward with CUDA events recorded on `stream`
+ * between its stages.  Blocks the host until the pass completes, then writes
+ * the stage durations in milliseconds: ms[0] input preparation (split or
+ * conversion; 0 for LEG_F64/LEG_F32), ms[1] Abel GEMM, ms[2] FFT stage.
+ * ms: host array of 3 floats.
+ */
+LEG_API int leg_forward_profiled(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream,
+                                 float *ms);
 
 /*
  * leg_backward -- df = L^T dc, the exact adjoint (transpose) of the linear
@@ -127,7 +143,7 @@ int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t str
  *   dc device, B x N (FP64 for LEG_F64, FP32 otherwise).
  *   df device, B x K (same type); overwritten.
  */
-int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaStream_t stream);
+LEG_API int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaStream_t stream);
 
 /*
  * leg_plain_forward -- the plain method: the Abel integral of a closed-form
@@ -140,11 +156,27 @@ int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaStream_t 
  */
 #define LEG_FAMILY_GENFN 0
 #define LEG_FAMILY_EXP   1
-int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
+LEG_API int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
                       double *c, cudaStream_t stream);
 
+/*
+ * leg_plan_status -- synchronise with the device and report whether any
+ * bounded device-side wait of this plan's tensor-core kernels expired since
+ * the last reset (LEG_ERR_TIMEOUT; the outputs of that call are invalid).
+ * reset != 0 clears the status word.  Blocks the host.
+ */
+LEG_API int leg_plan_status(leg_plan_t plan, int reset);
+
+/*
+ * leg_plan_set_wait_limit -- cycle budget of each bounded wait (mbarrier
+ * waits between the TMA, MMA and epilogue roles) in the tensor-core kernels;
+ * default 2e9 (about one second), or the environment variable
+ * LEG_WAIT_LIMIT_CYCLES at plan creation.  Teardown waits use a fixed budget.
+ */
+LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
+
 /* Message for the most recent failing call on this host thread ("" if none). */
-const char *leg_last_error(void);
+LEG_API const char *leg_last_error(void);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,222 @@
+"""GB300-native Legendre coefficients by the Abel-transform + FFT method.
+
+Thin Python binding of the C ABI in ``include/leg.h`` (libleg.so): argument
+marshalling only -- every step of the computation runs in the library's CUDA
+kernels.  PyTorch provides device memory and streams.
+
+Method: De Micheli & Viano, arXiv:1106.0463, Theorem 1 (Eq. 2.4, Eq. 2.5):
+c_n / (2n+1) are the nonnegative-index Fourier coefficients of the Abel-type
+transform of f, evaluated on an M-point periodic grid by Gauss-Legendre
+quadrature after the substitution x = cos y + s^2, followed by one FFT.
+
+The library must have been built (``python -c "import __graft_entry__ as g;
+g.build()"``); the first call into it raises ImportError otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+__all__ = [
+    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FAMILY_GENFN", "FAMILY_EXP",
+    "LegError", "Plan", "LegendreFn", "legendre", "library_path", "declared_symbols", "load_library",
+]
+
+F64, F32, BF16, SPLIT_FP16 = 0, 1, 2, 3
+FLAG_TAU_LITERAL = 1
+FAMILY_GENFN, FAMILY_EXP = 0, 1
+_ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libleg.so")
+_HEADER = os.path.join(os.path.dirname(_PKG), "include", "leg.h")
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def declared_symbols() -> list[str]:
+    """Names of every entry point declared (LEG_API) in include/leg.h."""
+    with open(_HEADER) as fh:
+        text = fh.read()
+    return re.findall(r"LEG_API\s+[\w\s\*]*?\b(leg_\w+)\s*\(", text)
+
+
+class LegError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("LEG_ERR_%s: %s" % (_ERR_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError("libleg.so is not built (%s); run __graft_entry__.build()" % _LIB_PATH)
+    lib = ctypes.CDLL(_LIB_PATH)
+    vp, i, u = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    sig = {
+        "leg_plan_create": ([ctypes.POINTER(vp), i, i, i, i, i], i),
+        "leg_plan_create_ex": ([ctypes.POINTER(vp), i, i, i, i, i, u], i),
+        "leg_plan_destroy": ([vp], i),
+        "leg_plan_reserve": ([vp, i], i),
+        "leg_plan_info": ([vp] + [ctypes.POINTER(i)] * 7, i),
+        "leg_forward": ([vp, vp, vp, i, vp], i),
+        "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
+        "leg_backward": ([vp, vp, vp, i, vp], i),
+        "leg_plain_forward": ([vp, i, vp, i, vp, vp], i),
+        "leg_plan_status": ([vp, i], i),
+        "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
+        "leg_last_error": ([], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+class _LazyLib:
+    """Loads libleg.so on first use and raises ImportError if it is missing."""
+
+    _handle = None
+
+    def __getattr__(self, name):
+        if _LazyLib._handle is None:
+            _LazyLib._handle = _load()
+        return getattr(_LazyLib._handle, name)
+
+
+_lib = _LazyLib()
+
+
+def load_library():
+    """Load libleg.so now (raises ImportError when it has not been built)."""
+    return _lib.leg_last_error
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise LegError(rc, _lib.leg_last_error().decode())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_tensor(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """An operator for one (N, M, K, Q, dtype); owns its device buffers.
+
+    N coefficients, M trapezoid points (power of two), K Chebyshev-Lobatto
+    samples per function, Q Gauss nodes per y-point (0: exact for degree K-1).
+    """
+
+    def __init__(self, N: int, M: int, K: int, Q: int = 0, dtype: int = SPLIT_FP16, flags: int = 0):
+        h = ctypes.c_void_p()
+        _check(_lib.leg_plan_create_ex(ctypes.byref(h), N, M, K, Q, dtype, flags))
+        self._h = h
+        vals = [ctypes.c_int() for _ in range(7)]
+        _check(_lib.leg_plan_info(h, *[ctypes.byref(v) for v in vals]))
+        self.N, self.M, self.K, self.Q, self.dtype, self.K_padded, self.rows = (v.value for v in vals)
+        self.flags = flags
+
+    @property
+    def io_dtype(self) -> torch.dtype:
+        return torch.float64 if self.dtype == F64 else torch.float32
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.leg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reserve(self, B: int):
+        _check(_lib.leg_plan_reserve(self._h, B))
+
+    def status(self, reset: bool = True):
+        """Raise LegError(TIMEOUT) if a bounded device wait expired (synchronises)."""
+        _check(_lib.leg_plan_status(self._h, int(bool(reset))))
+
+    def set_wait_limit(self, cycles: int):
+        _check(_lib.leg_plan_set_wait_limit(self._h, int(cycles)))
+
+    def forward(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """c = L f for f of shape (B, K) on the device (leg_forward)."""
+        B = f.shape[0] if f.dim() == 2 else -1
+        pf = _dev_tensor(f, self.io_dtype, (B, self.K), "f")
+        if c is None:
+            c = torch.empty((B, self.N), dtype=self.io_dtype, device=f.device)
+        pc = _dev_tensor(c, self.io_dtype, (B, self.N), "c")
+        _check(_lib.leg_forward(self._h, pf, pc, B, _stream(stream)))
+        return c
+
+    def forward_profiled(self, f: torch.Tensor, c: torch.Tensor, stream=None):
+        """Forward pass timed per stage (leg_forward_profiled); synchronises.
+
+        Returns (prep_ms, gemm_ms, fft_ms)."""
+        B = f.shape[0]
+        pf = _dev_tensor(f, self.io_dtype, (B, self.K), "f")
+        pc = _dev_tensor(c, self.io_dtype, (B, self.N), "c")
+        ms = (ctypes.c_float * 3)()
+        _check(_lib.leg_forward_profiled(self._h, pf, pc, B, _stream(stream), ms))
+        return tuple(float(v) for v in ms)
+
+    def backward(self, dc: torch.Tensor, df: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """df = L^T dc for dc of shape (B, N) (leg_backward)."""
+        B = dc.shape[0] if dc.dim() == 2 else -1
+        pdc = _dev_tensor(dc, self.io_dtype, (B, self.N), "dc")
+        if df is None:
+            df = torch.empty((B, self.K), dtype=self.io_dtype, device=dc.device)
+        pdf = _dev_tensor(df, self.io_dtype, (B, self.K), "df")
+        _check(_lib.leg_backward(self._h, pdc, pdf, B, _stream(stream)))
+        return df
+
+    def plain_forward(self, family: int, params: torch.Tensor, c: torch.Tensor | None = None,
+                      stream=None) -> torch.Tensor:
+        """Plain method for closed-form families (leg_plain_forward); FP64."""
+        B = params.shape[0]
+        pp = _dev_tensor(params, torch.float64, (B,), "params")
+        if c is None:
+            c = torch.empty((B, self.N), dtype=torch.float64, device=params.device)
+        pc = _dev_tensor(c, torch.float64, (B, self.N), "c")
+        _check(_lib.leg_plain_forward(self._h, family, pp, B, pc, _stream(stream)))
+        return c
+
+
+class LegendreFn(torch.autograd.Function):
+    """c = L f with the exact adjoint df = L^T dc as its backward."""
+
+    @staticmethod
+    def forward(ctx, f: torch.Tensor, plan: Plan):
+        ctx.plan = plan
+        return plan.forward(f.contiguous())
+
+    @staticmethod
+    def backward(ctx, dc: torch.Tensor):
+        return ctx.plan.backward(dc.contiguous()), None
+
+
+def legendre(f: torch.Tensor, plan: Plan) -> torch.Tensor:
+    """Differentiable Legendre coefficients of the rows of f (B x K CL samples)."""
+    return LegendreFn.apply(f, plan)

@@ -1,0 +1,323 @@
+// C ABI of libleg: plans, argument validation, workspace, dispatch.
+// The operations and their citations are documented in include/leg.h.
+#include <stdlib.h>
+
+#include <new>
+#include <string>
+
+#include "leg_internal.cuh"
+
+namespace {
+thread_local std::string g_last_error;
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+void free_workspace(leg_plan *p)
+{
+    cudaFree(p->G);
+    cudaFree(p->Gbar);
+    for (int s = 0; s < 3; ++s) {
+        cudaFree(p->Fh[s]);
+        p->Fh[s] = nullptr;
+    }
+    cudaFree(p->Fbf);
+    cudaFree(p->fexp);
+    p->G = p->Gbar = nullptr;
+    p->Fbf = nullptr;
+    p->fexp = nullptr;
+    p->ws_B = 0;
+}
+
+void free_plan(leg_plan *p)
+{
+    if (!p) return;
+    free_workspace(p);
+    cudaFree(p->omt2);
+    cudaFree(p->wq);
+    cudaFree(p->A64);
+    cudaFree(p->A32);
+    for (int s = 0; s < 3; ++s) cudaFree(p->Ah[s]);
+    for (int s = 0; s < 3; ++s) cudaFree(p->AhT[s]);
+    cudaFree(p->Abf);
+    cudaFree(p->rowexp);
+    cudaFree(p->colexp);
+    cudaFree(p->status);
+    cudaFree(p->tw64);
+    cudaFree(p->tw32);
+    cudaFree(p->twdf);
+    delete p;
+}
+
+size_t g_elem_bytes(int dtype)
+{
+    switch (dtype) {
+    case LEG_F64: return sizeof(double);
+    case LEG_SPLIT_FP16: return sizeof(float2);
+    default: return sizeof(float);
+    }
+}
+
+int ensure_workspace(leg_plan *p, int B)
+{
+    if (B <= p->ws_B) return LEG_OK;
+    free_workspace(p);
+    const size_t eb = g_elem_bytes(p->dtype);
+    const size_t Bz = (size_t)B;
+    const int rowsKp = leg_round_up(p->rows, 8);
+    const int bwdKp = (p->dtype == LEG_SPLIT_FP16) ? leg_round_up(rowsKp, LEG_KPAD) : 0;
+    p->ldg = (p->dtype == LEG_SPLIT_FP16) ? bwdKp : rowsKp;
+    LEG_CUDA_TRY(cudaMalloc(&p->G, eb * Bz * p->ldg));
+    LEG_CUDA_TRY(cudaMalloc(&p->Gbar, eb * Bz * p->ldg));
+    if (p->dtype == LEG_SPLIT_FP16) {
+        // input planes serve both directions: B x Kp (forward) or B x bwdKp (adjoint)
+        size_t w = (size_t)((p->Kp > bwdKp) ? p->Kp : bwdKp);
+        for (int s = 0; s < 3; ++s) LEG_CUDA_TRY(cudaMalloc(&p->Fh[s], sizeof(__half) * Bz * w));
+        LEG_CUDA_TRY(cudaMalloc(&p->fexp, sizeof(int) * Bz));
+    } else if (p->dtype == LEG_BF16) {
+        LEG_CUDA_TRY(cudaMalloc(&p->Fbf, sizeof(__nv_bfloat16) * Bz * p->Kp));
+    }
+    p->ws_B = B;
+    return LEG_OK;
+}
+
+int check_plan(leg_plan *p)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    int dev = -1;
+    LEG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "current device differs from the plan's device");
+    return LEG_OK;
+}
+}  // namespace
+
+int leg_set_error(int code, const std::string &msg)
+{
+    g_last_error = msg;
+    return code;
+}
+
+extern "C" const char *leg_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, int dtype, unsigned flags)
+{
+    if (!out) return leg_set_error(LEG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!is_pow2(M) || M < 8 || M > LEG_MAX_M)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "M must be a power of two in [8, 32768]");
+    if (N < 1 || N > M / 2)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "N must satisfy 1 <= N <= M/2");
+    if (K < 2 || K > LEG_MAX_K)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "K must be in [2, 16385]");
+    if (Q < 0 || Q > 16384)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "Q must be in [0, 16384]");
+    if (dtype < LEG_F64 || dtype > LEG_SPLIT_FP16)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "unknown dtype");
+    if (flags & ~LEG_FLAG_TAU_LITERAL)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "unknown flag");
+    if ((dtype == LEG_F64 || dtype == LEG_SPLIT_FP16) && M > 16384)
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "M > 16384 needs the FP32 transform in this build");
+
+    leg_plan *p = new (std::nothrow) leg_plan();
+    if (!p) return leg_set_error(LEG_ERR_OOM, "host allocation of the plan failed");
+    p->N = N;
+    p->M = M;
+    p->K = K;
+    p->Q = (Q == 0) ? (K + 1) / 2 : Q;
+    p->dtype = dtype;
+    p->flags = flags;
+    p->L = M / 2;
+    p->rows = M / 2 + 1;
+    p->Kp = leg_round_up(K, LEG_KPAD);
+    int rc = LEG_OK;
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return leg_set_error(LEG_ERR_CUDA, "cudaGetDevice failed");
+    }
+    if (const char *env = getenv("LEG_WAIT_LIMIT_CYCLES")) {
+        long long v = atoll(env);
+        if (v > 0) p->wait_limit = v;
+    }
+    if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
+        free_plan(p);
+        return leg_set_error(LEG_ERR_OOM, "status word allocation failed");
+    }
+    if ((rc = leg_build_twiddles(p)) != LEG_OK || (rc = leg_build_operator(p)) != LEG_OK) {
+        free_plan(p);
+        return rc;
+    }
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return leg_set_error(LEG_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_create(leg_plan_t *out, int N, int M, int K, int Q, int dtype)
+{
+    return leg_plan_create_ex(out, N, M, K, Q, dtype, 0u);
+}
+
+extern "C" int leg_plan_destroy(leg_plan_t plan)
+{
+    free_plan(plan);
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_reserve(leg_plan_t p, int B)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0");
+    return ensure_workspace(p, B);
+}
+
+extern "C" int leg_plan_info(leg_plan_t p, int *N, int *M, int *K, int *Q, int *dtype, int *Kp, int *rows)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (N) *N = p->N;
+    if (M) *M = p->M;
+    if (K) *K = p->K;
+    if (Q) *Q = p->Q;
+    if (dtype) *dtype = p->dtype;
+    if (Kp) *Kp = p->Kp;
+    if (rows) *rows = p->rows;
+    return LEG_OK;
+}
+
+namespace {
+// The forward pass; when ev != nullptr, events ev[0..3] are recorded on the
+// stream before the input preparation, the GEMM, the FFT, and after the FFT.
+int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, cudaEvent_t *ev)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return LEG_OK;
+    if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
+    if ((rc = ensure_workspace(p, B))) return rc;
+    if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[0], st));
+    switch (p->dtype) {
+    case LEG_F64:
+        if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+        rc = leg_gemm_f64_fwd(static_cast<const double *>(f), p->K, p->A64, p->K,
+                              static_cast<double *>(p->G), p->ldg, B, p->rows, p->K, st);
+        break;
+    case LEG_F32:
+        if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+        rc = leg_gemm_f32_fwd(static_cast<const float *>(f), p->K, p->A32, p->K,
+                              static_cast<float *>(p->G), p->ldg, B, p->rows, p->K, st);
+        break;
+    case LEG_SPLIT_FP16:
+        rc = leg_split_prepare_input(p, static_cast<const float *>(f), B, st);
+        if (!rc && ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+        if (!rc) rc = leg_gemm_split_fwd(p, B, st);
+        break;
+    case LEG_BF16:
+        rc = leg_bf16_prepare_input(p, static_cast<const float *>(f), B, st);
+        if (!rc && ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+        if (!rc) rc = leg_gemm_bf16_fwd(p, B, st);
+        break;
+    }
+    if (rc) return rc;
+    if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[2], st));
+    rc = leg_fft_forward(p, p->G, p->ldg, c, B, st);
+    if (rc) return rc;
+    if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[3], st));
+    return LEG_OK;
+}
+}  // namespace
+
+extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st)
+{
+    return forward_impl(p, f, c, B, st, nullptr);
+}
+
+extern "C" int leg_forward_profiled(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, float *ms)
+{
+    if (!ms) return leg_set_error(LEG_ERR_INVALID_ARG, "ms is NULL");
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int i = 0; i < 4; ++i) LEG_CUDA_TRY(cudaEventCreate(&ev[i]));
+    int rc = forward_impl(p, f, c, B, st, ev);
+    if (!rc && B > 0) {
+        cudaError_t e = cudaEventSynchronize(ev[3]);
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]);
+        if (e != cudaSuccess) rc = leg_set_error(LEG_ERR_CUDA, cudaGetErrorString(e));
+    } else if (!rc) {
+        ms[0] = ms[1] = ms[2] = 0.0f;
+    }
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+extern "C" int leg_backward(leg_plan_t p, const void *dc, void *df, int B, cudaStream_t st)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return LEG_OK;
+    if (!dc || !df) return leg_set_error(LEG_ERR_INVALID_ARG, "null dc or df");
+    if ((rc = ensure_workspace(p, B))) return rc;
+    if ((rc = leg_fft_adjoint(p, dc, p->Gbar, p->ldg, B, st))) return rc;
+    switch (p->dtype) {
+    case LEG_F64:
+        return leg_gemm_f64_adj(static_cast<const double *>(p->Gbar), p->ldg, p->A64, p->K,
+                                static_cast<double *>(df), p->K, B, p->rows, p->K, st);
+    case LEG_F32:
+        return leg_gemm_f32_adj(static_cast<const float *>(p->Gbar), p->ldg, p->A32, p->K,
+                                static_cast<float *>(df), p->K, B, p->rows, p->K, st);
+    case LEG_SPLIT_FP16:
+        return leg_gemm_split_adj(p, df, B, st);
+    default:
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "leg_backward is not available for LEG_BF16");
+    }
+}
+
+extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params, int B, double *c,
+                                 cudaStream_t st)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (family != LEG_FAMILY_GENFN && family != LEG_FAMILY_EXP)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "unknown family");
+    if (B < 0 || B > 65535) return leg_set_error(LEG_ERR_INVALID_ARG, "B must be in [0, 65535]");
+    if (B == 0) return LEG_OK;
+    if (!params || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null params or c");
+    if (p->M > 16384) return leg_set_error(LEG_ERR_UNSUPPORTED, "plain method limited to M <= 16384");
+    if ((rc = ensure_workspace(p, B))) return rc;
+    // the FP64 plain path needs 8-byte G elements; every dtype's G has at least
+    // B x ldg x 4 bytes, so use the backward buffer pair as one FP64 array when needed
+    double *G = nullptr;
+    int ldg = leg_round_up(p->rows, 8);
+    if (g_elem_bytes(p->dtype) >= sizeof(double)) {
+        G = static_cast<double *>(p->G);
+        ldg = p->ldg;
+    } else {
+        LEG_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&G), sizeof(double) * (size_t)B * ldg, st));
+    }
+    rc = leg_plain_g(p, family, params, B, G, ldg, st);
+    if (!rc) rc = leg_fft_forward_f64(p, G, ldg, c, B, st);
+    if (G != p->G) cudaFreeAsync(G, st);
+    return rc;
+}
+
+extern "C" int leg_plan_status(leg_plan_t p, int reset)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    int h = 0;
+    LEG_CUDA_TRY(cudaMemcpy(&h, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (reset && h) LEG_CUDA_TRY(cudaMemset(p->status, 0, sizeof(int)));
+    if (h & 1) return leg_set_error(LEG_ERR_TIMEOUT, "a bounded device-side wait expired");
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_set_wait_limit(leg_plan_t p, long long cycles)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (cycles < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "cycles < 0");
+    p->wait_limit = cycles;
+    return LEG_OK;
+}

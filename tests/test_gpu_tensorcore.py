@@ -1,0 +1,69 @@
+"""Parity of the tensor-core (tcgen05) paths with the FP64 CPU oracle.
+
+LEG_SPLIT_FP16 must stay within 1e-6 of the oracle (relative to max|c| per
+function); LEG_BF16 is a single BF16 product and is held to 5e-2.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+SMALL = [
+    (40, 128, 97, 0, 37),
+    (64, 256, 129, 20, 130),
+    (31, 64, 33, 5, 3),
+    (4, 8, 2, 1, 5),
+    (128, 256, 65, 0, 1),
+    (200, 512, 300, 0, 260),   # three function tiles, ragged rows/K
+]
+
+
+@pytest.fixture(scope="module")
+def leg():
+    import paper_1106_0463_gb300 as leg
+    assert torch.cuda.is_available()
+    return leg
+
+
+def relerr(c, ref):
+    c = np.atleast_2d(np.asarray(c, dtype=np.float64))
+    ref = np.atleast_2d(ref)
+    return float(np.max(np.max(np.abs(c - ref), axis=1) / np.max(np.abs(ref), axis=1)))
+
+
+def cheb_inputs(B, K, rho=(0.8, 0.99), seed=0):
+    f32, _, _ = workloads.random_chebyshev(B, K, rho, np.random.default_rng(seed))
+    return f32
+
+
+@pytest.mark.parametrize("N,M,K,Q,B", SMALL)
+def test_split_forward_matches_route2(leg, oracle, N, M, K, Q, B):
+    plan = leg.Plan(N, M, K, Q, leg.SPLIT_FP16)
+    f = cheb_inputs(B, K, seed=N + K)
+    c = plan.forward(torch.from_numpy(f).cuda())
+    plan.status()
+    ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f.astype(np.float64))
+    assert relerr(c.double().cpu().numpy(), ref) < 1e-6
+
+
+@pytest.mark.parametrize("N,M,K,Q,B", SMALL[:3])
+def test_bf16_forward_matches_route2(leg, oracle, N, M, K, Q, B):
+    plan = leg.Plan(N, M, K, Q, leg.BF16)
+    f = cheb_inputs(B, K, seed=N + K)
+    c = plan.forward(torch.from_numpy(f).cuda())
+    plan.status()
+    ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f.astype(np.float64))
+    assert relerr(c.double().cpu().numpy(), ref) < 5e-2
+
+
+def test_split_backward_is_the_transpose(leg, oracle):
+    N, M, K, Q, B = 24, 64, 33, 9, 5
+    plan = leg.Plan(N, M, K, Q, leg.SPLIT_FP16)
+    L = oracle.twisted_dft_matrix(N, M) @ oracle.abel_operator(M, K, Q, True)
+    v = np.random.default_rng(1).standard_normal((B, N)).astype(np.float32)
+    df = plan.backward(torch.from_numpy(v).cuda())
+    plan.status()
+    assert relerr(df.double().cpu().numpy(), v.astype(np.float64) @ L) < 1e-6

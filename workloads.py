@@ -63,12 +63,14 @@ def random_chebyshev(B: int, K: int, rho_range, rng: np.random.Generator):
 
 
 def workload_inputs(name: str, B: int | None = None, salt: int = 0):
-    """FP32 CL samples of a sampled workload (first B functions if B given)."""
+    """FP32 CL samples of a sampled workload.
+
+    Always draws the whole configured batch, so that the first B rows are the
+    same functions whatever B is requested."""
     cfg = CONFIGS[name]
-    Bw = cfg["B"] if B is None else B
     rng = rng_for(name, salt)
-    f32, coef, rho = random_chebyshev(Bw, cfg["K"], cfg["rho"], rng)
-    return f32
+    f32, coef, rho = random_chebyshev(cfg["B"], cfg["K"], cfg["rho"], rng)
+    return f32 if B is None else f32[:B]
 
 
 def loss_weights(N: int, rng: np.random.Generator):
