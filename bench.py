@@ -1,0 +1,376 @@
+"""Throughput benchmark of the Legendre-coefficient path on GB300.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--workload NAME] [--path split_fp16|f32|bf16|f64]
+
+One step = one forward pass of the sampled-input path over one batch with
+inputs resident in HBM: input split -> tcgen05 Abel GEMM -> twisted FFT with
+the (2n+1) scaling (leg_forward).  The default workload is B=4096 random
+decaying Chebyshev series at K=1025 Chebyshev-Lobatto nodes, N=512
+coefficients, M=2048 trapezoid points (exact tau rule), on the split-FP16 path
+whose error against the FP64 oracle is measured in the same run.
+
+Timing: W untimed warm-up steps; then, for each of K steps, L2 is flushed
+(a 512 MiB write) and the step is timed with CUDA events recorded by the
+library on the launch stream between its stages (leg_forward_profiled).
+Barrier + synchronize bracket the timed steps; the max over ranks is taken.
+Under torchrun (N > 1) every rank runs its own batch (weak scaling, no
+collective on the data path).
+
+--impl reference times the FP64 CPU oracle (the paper's method written out
+directly, route 2) on the host cores, on a bounded sample of the same
+workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads  # noqa: E402
+
+METRIC = "Legendre coeffs/sec (B*N/s) at <=1e-6 rel err vs FP64 oracle; % roofline vs plain FP64"
+UNIT = "coeffs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="cheb_b4096_k1025_n512_m2048")
+    ap.add_argument("--path", default="split_fp16", choices=["split_fp16", "f32", "bf16", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison paths")
+    return ap.parse_args()
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%s.csv" % gpu_index)
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() in ("active", "1", "yes"):
+                        reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ oracle (CPU)
+def oracle_rate(name: str, seconds: float = 12.0, max_fns: int = 256):
+    """Route 2 of the FP64 oracle on a bounded sample of the workload."""
+    from oracle import oracle as O
+    cfg = workloads.CONFIGS[name]
+    N, M, K = cfg["N"], cfg["M"], cfg["K"]
+    Q = O.exact_tau_points(K)
+    f = workloads.workload_inputs(name).astype(np.float64)
+    n = 2
+    t0 = time.time()
+    O.coeffs_abel(N, M, Q, f_cl=f[:n])
+    dt = time.time() - t0
+    # the cost is dominated by the per-point barycentric weights (shared by the
+    # functions of one call), so grow the sample while it fits the budget
+    while dt < seconds / 3 and n < max_fns:
+        n = min(max_fns, n * 4)
+        t0 = time.time()
+        O.coeffs_abel(N, M, Q, f_cl=f[:n])
+        dt = time.time() - t0
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return {"value": n * N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d of %d functions of %s, oracle route 2 (Abel + trapezoid, direct Fourier sum), "
+                      "FP64, OpenMP, %.2f s" % (n, cfg["B"], name, dt)}, n, dt
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    name = args.workload
+    cfg = workloads.CONFIGS[name]
+    from oracle import oracle as O
+    N, M, K = cfg["N"], cfg["M"], cfg["K"]
+    Q = O.exact_tau_points(K)
+    f = workloads.workload_inputs(name).astype(np.float64)
+    # size one step to about 2 s of CPU work
+    base, n, dt = oracle_rate(name, seconds=6.0, max_fns=64)
+    per_fn = dt / n
+    S = max(1, min(cfg["B"], int(2.0 / max(per_fn, 1e-9))))
+    for _ in range(args.warmup):
+        O.coeffs_abel(N, M, Q, f_cl=f[:S])
+    times = []
+    for i in range(args.steps):
+        lo = (i * S) % max(1, cfg["B"] - S + 1)
+        t0 = time.perf_counter()
+        O.coeffs_abel(N, M, Q, f_cl=f[lo:lo + S])
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = S * N / (ms / 1e3)
+    cores = base["cores"]
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": name, "B": cfg["B"], "K": K, "N": N, "M": M, "Q": Q,
+                   "path": "oracle route 2 (CPU)", "sample_per_step": S},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d functions per step of %s" % (S, name)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+PATHS = {"split_fp16": 3, "f32": 1, "bf16": 2, "f64": 0}
+DTYPE_STR = {
+    "split_fp16": "f16x3 split (6 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
+    "f32": "f32", "bf16": "bf16 (f32 accum) + f32 FFT", "f64": "f64",
+}
+
+
+def relerr(c, ref):
+    return float(np.max(np.max(np.abs(c - ref), 1) / np.max(np.abs(ref), 1)))
+
+
+def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0):
+    cfg = workloads.CONFIGS[name]
+    B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
+    dt = PATHS[path]
+    t0 = time.time()
+    plan = leg.Plan(N, M, K, 0, dt)
+    torch.cuda.synchronize()
+    plan_s = time.time() - t0
+    f_np = workloads.workload_inputs(name, salt=rank)
+    io = torch.float64 if dt == leg.F64 else torch.float32
+    f = torch.from_numpy(f_np).to(device="cuda", dtype=io)
+    c = torch.empty((B, N), dtype=io, device="cuda")
+    plan.reserve(B)
+    for _ in range(warmup):
+        plan.forward(f, c)
+    torch.cuda.synchronize()
+    stage = []
+    for _ in range(steps):
+        flush.zero_()
+        stage.append(plan.forward_profiled(f, c))
+    plan.status()
+    out = {"plan": plan, "f": f, "c": c, "f_np": f_np, "plan_s": plan_s, "stage": stage}
+    if sample_err:
+        out["c_sample"] = c[:sample_err].double().cpu().numpy()
+    return out
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    import paper_1106_0463_gb300 as leg
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    name = args.workload
+    cfg = workloads.CONFIGS[name]
+    B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
+    rows = M // 2 + 1
+    peaks, peak_src = load_peaks()
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    # ---------------- timed region: the selected path
+    barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    phys = vis.split(",")[local_rank].strip() if vis else str(local_rank)
+    clocks = ClockSampler(phys)
+    clocks.start()
+    res = run_path(leg, torch, name, args.path, rank, args.steps, args.warmup, flush, sample_err=16)
+    barrier()
+    clk = clocks.stop()
+    stage = np.array(res["stage"])              # steps x 3 (ms)
+    step_ms = stage.sum(1)
+    total_ms = float(step_ms.sum())
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = world * B * N / (ms_per_step / 1e3)
+    prep_ms, gemm_ms, fft_ms = (float(v) for v in stage.mean(0))
+
+    # ---------------- e2e through the public API with pinned host buffers
+    plan, f, c = res["plan"], res["f"], res["c"]
+    f_host = torch.from_numpy(res["f_np"]).to(f.dtype).pin_memory()
+    c_host = torch.empty(c.shape, dtype=c.dtype).pin_memory()
+    st = torch.cuda.current_stream()
+    e2e_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        f.copy_(f_host, non_blocking=True)
+        plan.forward(f, c)
+        c_host.copy_(c, non_blocking=True)
+        e1.record(st)
+        e1.synchronize()
+        if i >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e_step = statistics.mean(e2e_ms)
+    if dist is not None:
+        t = torch.tensor([e2e_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_step = float(t.item())
+    e2e = {"value": world * B * N / (e2e_step / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
+           "d2h_bytes_per_step": c_host.numel() * c_host.element_size()}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # ---------------- parity on sampled functions (oracle, CPU)
+    from oracle import oracle as O
+    ref = O.coeffs_abel(N, M, O.exact_tau_points(K), f_cl=res["f_np"][:16].astype(np.float64))
+    err = relerr(res["c_sample"], ref)
+
+    # ---------------- roofline of the dominant kernel
+    flops_useful = 2.0 * B * rows * K                      # per GEMM launch (distinct rows, eq. 2.12)
+    products = {"split_fp16": 6, "bf16": 1, "f32": 1, "f64": 1}[args.path]
+    fft_bytes = B * rows * (8 if args.path in ("split_fp16", "f64") else 4) + B * N * (8 if args.path == "f64" else 4)
+    prep_bytes = B * K * 4 + 3 * B * ((K + 63) // 64 * 64) * 2 + B * 4
+    kernels = {"abel_gemm": gemm_ms, "fft": fft_ms, "input_split": prep_ms}
+    dom = max(kernels, key=kernels.get)
+    peak_tensor = peaks.get("bf16_tflops", 1899.1)
+    if dom == "abel_gemm" and args.path in ("split_fp16", "bf16"):
+        achieved = flops_useful / (gemm_ms / 1e3) / 1e12
+        roof = {"kernel": "tc_gemm_kernel (Abel GEMM)", "bound": "tensor", "achieved": achieved,
+                "peak": peak_tensor, "unit": "TFLOP/s", "frac": achieved / peak_tensor, "traffic": None,
+                "flops_per_launch": flops_useful, "executed_flops_per_launch": products * 2.0 * B * rows *
+                ((K + 63) // 64 * 64), "peak_source": "%s bf16_tflops (fp16 dense rate equals bf16)" % peak_src}
+    else:
+        nm = dom
+        by = {"fft": fft_bytes, "input_split": prep_bytes, "abel_gemm": B * K * 4 + rows * K * 4 + B * rows * 4}[nm]
+        achieved = by / (kernels[nm] / 1e3) / 1e9
+        roof = {"kernel": nm, "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6696.2),
+                "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6696.2), "traffic": None,
+                "bytes_per_launch": by, "peak_source": "%s hbm_gbs" % peak_src}
+    stages = {
+        "input_split": {"ms": prep_ms, "bytes": prep_bytes,
+                        "gbs": prep_bytes / (prep_ms / 1e3) / 1e9 if prep_ms > 0 else None},
+        "abel_gemm": {"ms": gemm_ms, "useful_tflops": flops_useful / (gemm_ms / 1e3) / 1e12,
+                      "executed_tflops": products * flops_useful / (gemm_ms / 1e3) / 1e12},
+        "fft": {"ms": fft_ms, "bytes": fft_bytes, "gbs": fft_bytes / (fft_ms / 1e3) / 1e9},
+    }
+
+    extras = {}
+    if not args.no_extras and args.path != "f64":
+        for p_name, st_n in (("f64", 3), ("f32", 5)):
+            if p_name == args.path:
+                continue
+            r = run_path(leg, torch, name, p_name, rank, st_n, 2, flush, sample_err=16)
+            ms = float(np.array(r["stage"]).sum(1).mean())
+            extras[p_name + "_gpu_path"] = {"value": B * N / (ms / 1e3), "ms_per_step": ms,
+                                            "max_rel_err": relerr(r["c_sample"], ref)}
+            del r
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu, _, _ = oracle_rate(name)
+    launches_per_step = {"split_fp16": 3, "bf16": 3, "f32": 2, "f64": 2}[args.path]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": DTYPE_STR[args.path], "data": "synthetic",
+        "config": {"workload": name, "B": B, "K": K, "N": N, "M": M, "Q": (K + 1) // 2, "path": args.path,
+                   "l2": "flushed (512 MiB write) before every timed step",
+                   "inputs": "random decaying Chebyshev series sampled at CL nodes, FP32, seeded"},
+        "max_rel_err": err, "err_sample": "16 functions vs FP64 oracle route 2",
+        "roofline": roof, "stages": stages, "plan_build_s": res["plan_s"],
+        "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
+        "cpu_baseline": cpu,
+    }
+    if extras:
+        line.update(extras)
+        if "f64_gpu_path" in extras:
+            line["speedup_vs_fp64_gpu_path"] = value / world / extras["f64_gpu_path"]["value"]
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    gpu_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()
