@@ -175,6 +175,28 @@ LEG_API int leg_plan_status(leg_plan_t plan, int reset);
  */
 LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
 
+/*
+ * leg_forward_noalloc -- leg_forward for a LEG_SPLIT_FP16 plan that allocates
+ * no device memory.  (The paper has no counterpart: this is a library
+ * convenience.)  It is meant for callers that must not allocate at call time,
+ * such as a host framework that owns the whole device-memory budget through
+ * its own fixed pool, or a latency-critical caller that cannot afford the
+ * host blocking and device synchronisation that cudaMalloc/cudaFree may
+ * cause.  The plan is created (and allocates) beforehand, as usual.
+ *   f  device, B x K FP32;  c  device, B x N FP32 (as leg_forward).
+ * The intermediate buffers (input slices, per-function scales, the Abel
+ * GEMM result) come from one static device array of 64 MiB in the library,
+ * which every GPU that loads the library keeps reserved until process exit.
+ * A batch needing more scratch than that (about B*(6*Kp + 8*Mr) bytes, Kp = K
+ * rounded up to 64, Mr = M/2+1 rounded up to 64) is rejected with
+ * LEG_ERR_INVALID_ARG and a message stating the sizes.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array and it keeps the last call's contents: calls whose work
+ * overlaps on the GPU race on it, so serialise them.
+ */
+LEG_API int leg_forward_noalloc(leg_plan_t plan, const float *f, float *c, int B, cudaStream_t stream);
+
 /* Message for the most recent failing call on this host thread ("" if none). */
 LEG_API const char *leg_last_error(void);
 

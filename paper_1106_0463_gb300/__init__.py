@@ -66,6 +66,7 @@ def _load():
         "leg_forward": ([vp, vp, vp, i, vp], i),
         "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_backward": ([vp, vp, vp, i, vp], i),
+        "leg_forward_noalloc": ([vp, vp, vp, i, vp], i),
         "leg_plain_forward": ([vp, i, vp, i, vp, vp], i),
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
@@ -169,6 +170,17 @@ class Plan:
             c = torch.empty((B, self.N), dtype=self.io_dtype, device=f.device)
         pc = _dev_tensor(c, self.io_dtype, (B, self.N), "c")
         _check(_lib.leg_forward(self._h, pf, pc, B, _stream(stream)))
+        return c
+
+    def forward_noalloc(self, f: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:
+        """leg_forward_noalloc: the split-FP16 forward pass for callers that
+        must not allocate device memory at call time; its intermediates live in
+        the library's static 64 MiB device scratch (shared by all calls on a
+        device, so overlapping calls race).  c must be preallocated."""
+        B = f.shape[0] if f.dim() == 2 else -1
+        pf = _dev_tensor(f, torch.float32, (B, self.K), "f")
+        pc = _dev_tensor(c, torch.float32, (B, self.N), "c")
+        _check(_lib.leg_forward_noalloc(self._h, pf, pc, B, _stream(stream)))
         return c
 
     def forward_profiled(self, f: torch.Tensor, c: torch.Tensor, stream=None):

@@ -455,3 +455,25 @@ int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st)
     return launch_tc<1, false>(maps, B, p->rows, p->Kp, nullptr, nullptr, p->G, p->ldg, p->status,
                                p->wait_limit, st);
 }
+
+// Variants of the split forward launchers that take their buffers explicitly
+// (used by leg_forward_noalloc, whose buffers live in a static device array).
+int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, __half *const planes[3], int *fexp,
+                                 cudaStream_t st)
+{
+    split_rows_kernel<float><<<B, 256, 0, st>>>(f, p->K, p->K, p->Kp, planes[0], planes[1], planes[2], fexp);
+    LEG_LAUNCH_CHECK("split_rows_kernel");
+    return LEG_OK;
+}
+
+int leg_gemm_split_fwd_into(leg_plan *p, int B, __half *const planes[3], const int *fexp, float2 *G, int ldg,
+                            cudaStream_t st)
+{
+    TcMaps maps;
+    int rc;
+    for (int s = 0; s < 3; ++s) {
+        if ((rc = make_map(&maps.x[s], planes[s], p->Kp, B, p->Kp, false))) return rc;
+        if ((rc = make_map(&maps.w[s], p->Ah[s], p->Kp, p->rows, p->Kp, false))) return rc;
+    }
+    return launch_tc<6, true>(maps, B, p->rows, p->Kp, fexp, p->rowexp, G, ldg, p->status, p->wait_limit, st);
+}

@@ -135,3 +135,7 @@ int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st);
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st);
 int leg_build_split_transposed(leg_plan *p);
+int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, __half *const planes[3], int *fexp,
+                                 cudaStream_t st);
+int leg_gemm_split_fwd_into(leg_plan *p, int B, __half *const planes[3], const int *fexp, float2 *G, int ldg,
+                            cudaStream_t st);
