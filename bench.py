@@ -180,7 +180,7 @@ def reference_arm(args, rank, world):
 # ------------------------------------------------------------------ GPU arm
 PATHS = {"split_fp16": 3, "f32": 1, "bf16": 2, "f64": 0}
 DTYPE_STR = {
-    "split_fp16": "f16x3 split (6 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
+    "split_fp16": "f16x3 split (8 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
     "f32": "f32", "bf16": "bf16 (f32 accum) + f32 FFT", "f64": "f64",
 }
 
@@ -296,7 +296,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---------------- roofline of the dominant kernel
     flops_useful = 2.0 * B * rows * K                      # per GEMM launch (distinct rows, eq. 2.12)
-    products = {"split_fp16": 6, "bf16": 1, "f32": 1, "f64": 1}[args.path]
+    products = {"split_fp16": 8, "bf16": 1, "f32": 1, "f64": 1}[args.path]
     fft_bytes = B * rows * (8 if args.path in ("split_fp16", "f64") else 4) + B * N * (8 if args.path == "f64" else 4)
     prep_bytes = B * K * 4 + 3 * B * ((K + 63) // 64 * 64) * 2 + B * 4
     kernels = {"abel_gemm": gemm_ms, "fft": fft_ms, "input_split": prep_ms}

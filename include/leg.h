@@ -64,10 +64,10 @@ extern "C" {
  *                  FP32 accumulation (tcgen05), FP32 FFT.
  *   LEG_SPLIT_FP16 f, c in FP32; operator and input each split into three
  *                  FP16 slices (a fixed-point leading slice, two residual
- *                  slices), six tcgen05 products into three FP32 TMEM
+ *                  slices), eight tcgen05 products into four FP32 TMEM
  *                  accumulators of which the leading one is exact, combined
  *                  into a double-float result; double-float FFT.  The path
- *                  that meets a 1e-6 relative error.
+ *                  aimed at a 1e-6 relative error.
  */
 typedef enum {
     LEG_F64 = 0,
@@ -100,6 +100,14 @@ typedef struct leg_plan *leg_plan_t;
  */
 LEG_API int leg_plan_create(leg_plan_t *out, int N, int M, int K, int Q, int dtype);
 LEG_API int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, int dtype, unsigned flags);
+
+/*
+ * leg_plan_create_like -- a plan of another dtype for the same (N, M, K, Q,
+ * flags) as src, reusing src's FP64 operator (a device copy) instead of
+ * building it again; only the operand planes of the new dtype are derived.
+ * Synchronises the host with the device.  Errors as leg_plan_create.
+ */
+LEG_API int leg_plan_create_like(leg_plan_t *out, leg_plan_t src, int dtype);
 
 /* Releases every device buffer of the plan.  NULL is accepted. */
 LEG_API int leg_plan_destroy(leg_plan_t plan);

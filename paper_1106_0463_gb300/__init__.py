@@ -60,6 +60,7 @@ def _load():
     sig = {
         "leg_plan_create": ([ctypes.POINTER(vp), i, i, i, i, i], i),
         "leg_plan_create_ex": ([ctypes.POINTER(vp), i, i, i, i, i, u], i),
+        "leg_plan_create_like": ([ctypes.POINTER(vp), vp, i], i),
         "leg_plan_destroy": ([vp], i),
         "leg_plan_reserve": ([vp, i], i),
         "leg_plan_info": ([vp] + [ctypes.POINTER(i)] * 7, i),
@@ -128,14 +129,24 @@ class Plan:
     samples per function, Q Gauss nodes per y-point (0: exact for degree K-1).
     """
 
-    def __init__(self, N: int, M: int, K: int, Q: int = 0, dtype: int = SPLIT_FP16, flags: int = 0):
+    def __init__(self, N: int, M: int, K: int, Q: int = 0, dtype: int = SPLIT_FP16, flags: int = 0,
+                 like: "Plan | None" = None):
         h = ctypes.c_void_p()
-        _check(_lib.leg_plan_create_ex(ctypes.byref(h), N, M, K, Q, dtype, flags))
+        if like is not None:
+            _check(_lib.leg_plan_create_like(ctypes.byref(h), like._h, dtype))
+            flags = like.flags
+        else:
+            _check(_lib.leg_plan_create_ex(ctypes.byref(h), N, M, K, Q, dtype, flags))
         self._h = h
         vals = [ctypes.c_int() for _ in range(7)]
         _check(_lib.leg_plan_info(h, *[ctypes.byref(v) for v in vals]))
         self.N, self.M, self.K, self.Q, self.dtype, self.K_padded, self.rows = (v.value for v in vals)
         self.flags = flags
+
+    @classmethod
+    def like(cls, src: "Plan", dtype: int) -> "Plan":
+        """Same sizes as src with another dtype, reusing src's operator (leg_plan_create_like)."""
+        return cls(src.N, src.M, src.K, src.Q, dtype, like=src)
 
     @property
     def io_dtype(self) -> torch.dtype:

@@ -115,8 +115,6 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown dtype");
     if (flags & ~LEG_FLAG_TAU_LITERAL)
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown flag");
-    if ((dtype == LEG_F64 || dtype == LEG_SPLIT_FP16) && M > 16384)
-        return leg_set_error(LEG_ERR_UNSUPPORTED, "M > 16384 needs the FP32 transform in this build");
 
     leg_plan *p = new (std::nothrow) leg_plan();
     if (!p) return leg_set_error(LEG_ERR_OOM, "host allocation of the plan failed");
@@ -150,6 +148,48 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
     if (e != cudaSuccess) {
         free_plan(p);
         return leg_set_error(LEG_ERR_CUDA, std::string("plan build: ") + cudaGetErrorString(e));
+    }
+    *out = p;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_create_like(leg_plan_t *out, leg_plan_t src, int dtype)
+{
+    if (!out) return leg_set_error(LEG_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int rc = check_plan(src);
+    if (rc) return rc;
+    if (dtype < LEG_F64 || dtype > LEG_SPLIT_FP16) return leg_set_error(LEG_ERR_INVALID_ARG, "unknown dtype");
+    leg_plan *p = new (std::nothrow) leg_plan();
+    if (!p) return leg_set_error(LEG_ERR_OOM, "host allocation of the plan failed");
+    p->N = src->N;
+    p->M = src->M;
+    p->K = src->K;
+    p->Q = src->Q;
+    p->dtype = dtype;
+    p->flags = src->flags;
+    p->L = src->L;
+    p->rows = src->rows;
+    p->Kp = src->Kp;
+    p->device = src->device;
+    p->wait_limit = src->wait_limit;
+    auto fail = [&](int code, const char *what) {
+        free_plan(p);
+        return leg_set_error(code, what);
+    };
+    if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
+        return fail(LEG_ERR_OOM, "status word allocation failed");
+    if (cudaMalloc(&p->omt2, sizeof(double) * p->Q) != cudaSuccess ||
+        cudaMalloc(&p->wq, sizeof(double) * p->Q) != cudaSuccess ||
+        cudaMalloc(&p->A64, sizeof(double) * (size_t)p->rows * p->K) != cudaSuccess)
+        return fail(LEG_ERR_OOM, "operator allocation failed");
+    if (cudaMemcpy(p->omt2, src->omt2, sizeof(double) * p->Q, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(p->wq, src->wq, sizeof(double) * p->Q, cudaMemcpyDeviceToDevice) != cudaSuccess ||
+        cudaMemcpy(p->A64, src->A64, sizeof(double) * (size_t)p->rows * p->K, cudaMemcpyDeviceToDevice) != cudaSuccess)
+        return fail(LEG_ERR_CUDA, "operator copy failed");
+    if ((rc = leg_build_twiddles(p)) != LEG_OK || (rc = leg_build_planes(p)) != LEG_OK) {
+        free_plan(p);
+        return rc;
     }
     *out = p;
     return LEG_OK;
@@ -285,7 +325,6 @@ extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params,
     if (B < 0 || B > 65535) return leg_set_error(LEG_ERR_INVALID_ARG, "B must be in [0, 65535]");
     if (B == 0) return LEG_OK;
     if (!params || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null params or c");
-    if (p->M > 16384) return leg_set_error(LEG_ERR_UNSUPPORTED, "plain method limited to M <= 16384");
     if ((rc = ensure_workspace(p, B))) return rc;
     // the FP64 plain path needs 8-byte G elements; every dtype's G has at least
     // B x ldg x 4 bytes, so use the backward buffer pair as one FP64 array when needed

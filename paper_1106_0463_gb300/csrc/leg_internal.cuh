@@ -45,11 +45,12 @@ constexpr int LEG_MAX_M = 32768;
 constexpr int LEG_MAX_K = 16385;
 
 // Split-FP16 scheme (fixed-point leading slice): granularity exponents of the
-// leading slices of the operator (A0 on a 2^-14 grid) and of the input
-// (F0 on a 2^-9 grid); products A0*F0 lie on a 2^-23 grid and every partial
-// sum stays below 2 in magnitude, so their FP32 accumulation is exact.
-constexpr int LEG_SPLIT_ABITS = 14;
-constexpr int LEG_SPLIT_FBITS = 9;
+// leading slices of the operator (A0 on a 2^-16 grid) and of the input
+// (F0 on a 2^-7 grid); products A0*F0 lie on a 2^-23 grid and every partial
+// sum stays below 2 in magnitude, so their FP32 accumulation is exact.  The
+// residual slices carry weights 2^-7 and 2^-14 (LEG_SPLIT_FBITS per level).
+constexpr int LEG_SPLIT_ABITS = 16;
+constexpr int LEG_SPLIT_FBITS = 7;
 
 // ---------------------------------------------------------------------------
 // Plan.
@@ -101,7 +102,8 @@ struct leg_plan {
 // Launchers (each returns a LEG_* status).
 // ---------------------------------------------------------------------------
 // operator build (leg_operator.cu)
-int leg_build_operator(leg_plan *p);
+int leg_build_operator(leg_plan *p);   // FP64 operator, then leg_build_planes
+int leg_build_planes(leg_plan *p);
 int leg_build_twiddles(leg_plan *p);
 
 // SIMT GEMMs (leg_gemm_simt.cu)

@@ -168,12 +168,11 @@ __global__ void plane_bf16_kernel(const double *A, int K, int Kp, __nv_bfloat16 
 }
 
 // Split-FP16 planes of row j.  Row scale 2^e_j >= sum_k |A[j,k]| (so the
-// scaled row has L1 norm <= 1).  With a = A[j,k] / 2^e_j:
-//   A0 = a rounded to FP16 but never finer than 2^-14 (a fixed-point grid
-//        for |a| < 2^-4, ordinary FP16 rounding above),
-//   r1 = (a - A0) 2^9,  A1 = fp16(r1),
-//   r2 = (r1 - A1) 2^11, A2s = fp16(r2 / 4),
-// so a = A0 + 2^-9 A1 + 2^-18 A2s + O(2^-42).
+// scaled row has L1 norm <= 1).  With a = A[j,k] / 2^e_j, s = LEG_SPLIT_FBITS:
+//   A0 = a rounded to FP16 but never finer than 2^-LEG_SPLIT_ABITS (a
+//        fixed-point grid for small |a|, ordinary FP16 rounding above),
+//   r1 = (a - A0) 2^s,  A1 = fp16(r1),  A2s = fp16((r1 - A1) 2^s),
+// so a = A0 + 2^-s A1 + 2^-2s A2s up to the FP16 rounding of A2s.
 __global__ void plane_split_kernel(const double *A, int K, int Kp, __half *A0p, __half *A1p,
                                    __half *A2p, int *rowexp)
 {
@@ -202,12 +201,11 @@ __global__ void plane_split_kernel(const double *A, int K, int Kp, __half *A0p, 
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double a = (k < K) ? A[(size_t)j * K + k] * inv : 0.0;
         double a0;
-        if (fabs(a) >= 0.0625) a0 = (double)__double2half(a);
+        if (fabs(a) >= ldexp(1.0, 10 - LEG_SPLIT_ABITS)) a0 = (double)__double2half(a);   // FP16 ulp >= grid
         else a0 = rint(ldexp(a, LEG_SPLIT_ABITS)) * ldexp(1.0, -LEG_SPLIT_ABITS);
         double r1 = ldexp(a - a0, LEG_SPLIT_FBITS);
         __half h1 = __double2half(r1);
-        double r2 = ldexp(r1 - (double)h1, 11);
-        __half h2 = __double2half(ldexp(r2, -2));
+        __half h2 = __double2half(ldexp(r1 - (double)h1, LEG_SPLIT_FBITS));
         size_t o = (size_t)j * Kp + k;
         A0p[o] = __double2half(a0);
         A1p[o] = h1;
@@ -247,7 +245,6 @@ int leg_build_operator(leg_plan *p)
     const int n_half = (n_rule + 1) / 2;
 
     double *xh = nullptr, *wh = nullptr, *omxk = nullptr, *lam = nullptr;
-    int rc = LEG_OK;
     auto cleanup = [&]() {
         cudaFree(xh); cudaFree(wh); cudaFree(omxk); cudaFree(lam);
     };
@@ -278,7 +275,25 @@ int leg_build_operator(leg_plan *p)
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     abel_operator_kernel<<<rows, 256, smem>>>(p->M, K, Q, omt2, wq, omxk, lam, p->A64);
     LEG_TRY_CLEAN(cudaGetLastError());
+    cleanup();
+#undef LEG_TRY_CLEAN
+    return leg_build_planes(p);
+}
 
+// Operand planes of the plan's dtype, derived from the FP64 operator.
+int leg_build_planes(leg_plan *p)
+{
+    const int K = p->K, rows = p->rows;
+    auto cleanup = []() {};
+#define LEG_TRY_CLEAN(expr)                                                         \
+    do {                                                                            \
+        cudaError_t _e = (expr);                                                    \
+        if (_e != cudaSuccess) {                                                    \
+            cleanup();                                                              \
+            return leg_set_error(_e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA, \
+                                 std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+        }                                                                           \
+    } while (0)
     if (p->dtype == LEG_F32) {
         size_t n = (size_t)rows * K;
         LEG_TRY_CLEAN(cudaMalloc(&p->A32, sizeof(float) * n));
@@ -300,7 +315,6 @@ int leg_build_operator(leg_plan *p)
     }
     LEG_TRY_CLEAN(cudaGetLastError());
     LEG_TRY_CLEAN(cudaDeviceSynchronize());
-    cleanup();
 #undef LEG_TRY_CLEAN
-    return rc;
+    return LEG_OK;
 }

@@ -134,6 +134,21 @@ __device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, float (&v)[32
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major tile stored in the 128-byte
@@ -148,6 +163,19 @@ __device__ __forceinline__ uint64_t desc_k_sw128(uint32_t smem_addr)
     d |= (uint64_t)(1024u >> 4) << 32;                   // stride byte offset: 8 rows x 128 B
     d |= (uint64_t)1u << 46;                             // descriptor version (sm_100 family)
     d |= (uint64_t)2u << 61;                             // layout: 128-byte swizzle
+    return d;
+}
+
+// Same for the 64-byte swizzle layout (CU_TENSOR_MAP_SWIZZLE_64B): rows of
+// 32 16-bit elements (64 B), 8-row atoms 512 B apart; tile base 512-byte aligned.
+__device__ __forceinline__ uint64_t desc_k_sw64(uint32_t smem_addr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);        // start address
+    d |= (uint64_t)1u << 16;                             // leading byte offset (unused for this layout)
+    d |= (uint64_t)(512u >> 4) << 32;                    // stride byte offset: 8 rows x 64 B
+    d |= (uint64_t)1u << 46;                             // descriptor version (sm_100 family)
+    d |= (uint64_t)4u << 61;                             // layout: 64-byte swizzle
     return d;
 }
 

@@ -86,17 +86,39 @@ SMALL = [
     (31, 64, 33, 5, 3),
     (4, 8, 2, 1, 5),        # degenerate: smallest grid, linear f
     (128, 256, 65, 0, 1),   # N = M/2
+    (8192, 32768, 65, 0, 3),   # largest grid: M = 32768, N = M/4
 ]
 
 
 @pytest.mark.parametrize("dtype", [0, 1])
-@pytest.mark.parametrize("N,M,K,Q,B", SMALL)
+@pytest.mark.parametrize("N,M,K,Q,B", SMALL[:5])
 def test_forward_matches_route2(leg, oracle, dtype, N, M, K, Q, B):
     plan = leg.Plan(N, M, K, Q, dtype)
     f = cheb_inputs(B, K, seed=N + K)
     c = run_forward(leg, plan, f)
     ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f.astype(np.float64))
     assert relerr(c, ref) < TOL[dtype]
+
+
+def test_forward_f64_largest_grid(leg, oracle):
+    N, M, K, Q, B = SMALL[5]
+    plan = leg.Plan(N, M, K, Q, leg.F64)
+    f = cheb_inputs(B, K, seed=7)
+    c = run_forward(leg, plan, f)
+    ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f.astype(np.float64))
+    assert relerr(c, ref) < 1e-11
+
+
+def test_plain_method_largest_grid(leg):
+    N, M, Q = 8192, 32768, 1024
+    plan = leg.Plan(N, M, 2, Q, leg.F64)
+    t = torch.tensor([0.95, 0.5], dtype=torch.float64, device="cuda")
+    c = plan.plain_forward(leg.FAMILY_GENFN, t).cpu().numpy()
+    n = np.arange(N)
+    # aliasing of the trapezoid rule is ~t^(M - N) (negligible); FP64 rounding,
+    # amplified by (2n+1) up to n = 8191, stays within the FP64 tolerance
+    assert np.max(np.abs(c[1] - 0.5 ** n)) < 1e-11
+    assert np.max(np.abs(c[0] - 0.95 ** n)) < 1e-9
 
 
 def test_forward_f64_exact_config_equals_route1(leg, oracle):

@@ -18,6 +18,7 @@ SMALL = [
     (4, 8, 2, 1, 5),
     (128, 256, 65, 0, 1),
     (200, 512, 300, 0, 260),   # three function tiles, ragged rows/K
+    (8192, 32768, 65, 0, 3),   # largest grid (M = 32768)
 ]
 
 
