@@ -216,6 +216,69 @@ def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0):
     return out
 
 
+def time_steps(torch, fn, flush, steps, warmup):
+    """Mean CUDA-event time (ms) of fn() over `steps` calls, L2 flushed before each."""
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts)
+
+
+def extra_workloads(leg, torch, flush, rank):
+    """The other workloads of the method, measured on the split path."""
+    out = {}
+    # ragged batch: 10,000 closed-form functions, N log-uniform in [32, 8192]
+    cfg = workloads.CONFIGS["ragged_10000"]
+    rng = np.random.default_rng(workloads.SEED_BASE + 3 + 1000 * rank)
+    fam, par, n = workloads.ragged_spec(cfg["count"], rng, cfg["Nmin"], cfg["Nmax"])
+    lay = workloads.ragged_layout(fam, par, n, rng)
+    t0 = time.time()
+    plans = [leg.Plan(*workloads.bucket_sizes(Nb), dtype=leg.SPLIT_FP16) for Nb in lay["buckets"]]
+    batch = leg.Ragged(plans, lay["bidx"], n, lay["in_off"], lay["out_off"])
+    torch.cuda.synchronize()
+    setup = time.time() - t0
+    dev = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")
+    f = torch.empty(lay["n_in"], dtype=torch.float32, device="cuda")
+    leg.sample_cl(dev(fam, torch.int32), dev(par, torch.float64), dev(lay["K"], torch.int32),
+                  dev(lay["in_off"], torch.int64), f, coef=dev(lay["coef"], torch.float64),
+                  coef_off=dev(lay["coef_off"], torch.int64))
+    c = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
+    ms = time_steps(torch, lambda: batch.forward(f, c), flush, 10, 3)
+    batch.status()
+    out["ragged_10000"] = {"value": float(np.sum(n)) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                           "functions": cfg["count"], "coefficients": int(np.sum(n)),
+                           "buckets": lay["buckets"], "plan_build_s": setup,
+                           "launches_per_step": 2 + len(lay["buckets"]), "cuda_graph": True}
+    del batch, plans, f, c
+    # differentiation workload: forward + backward on the split path
+    name = "cheb_b1024_k4097_n2048_m8192"
+    cf = workloads.CONFIGS[name]
+    plan = leg.Plan(cf["N"], cf["M"], cf["K"], 0, leg.SPLIT_FP16)
+    x = torch.from_numpy(workloads.workload_inputs(name)).cuda()
+    cc = torch.empty((cf["B"], cf["N"]), dtype=torch.float32, device="cuda")
+    df = torch.empty_like(x)
+    plan.reserve(cf["B"])
+
+    def fwd_bwd():
+        plan.forward(x, cc)
+        plan.backward(cc, df)
+    ms = time_steps(torch, fwd_bwd, flush, 10, 3)
+    plan.status()
+    out["differentiation_b1024_k4097_n2048_m8192"] = {
+        "value": cf["B"] * cf["N"] / (ms / 1e3), "unit": UNIT + " (forward + backward)", "ms_per_step": ms}
+    del plan, x, cc, df
+    return out
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import paper_1106_0463_gb300 as leg
@@ -333,6 +396,8 @@ def gpu_arm(args, rank, world, local_rank):
             extras[p_name + "_gpu_path"] = {"value": B * N / (ms / 1e3), "ms_per_step": ms,
                                             "max_rel_err": relerr(r["c_sample"], ref)}
             del r
+    if not args.no_extras:
+        extras.update(extra_workloads(leg, torch, flush, rank))
     cpu = None
     if not args.no_cpu_baseline:
         cpu, _, _ = oracle_rate(name)

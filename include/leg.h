@@ -164,8 +164,56 @@ LEG_API int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaS
  */
 #define LEG_FAMILY_GENFN 0
 #define LEG_FAMILY_EXP   1
+#define LEG_FAMILY_CHEB  2   /* leg_sample_cl only: sum_m coef_m T_m(x) */
 LEG_API int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
                       double *c, cudaStream_t stream);
+
+/*
+ * Ragged batches (functions of different sizes, grouped in size buckets).
+ *
+ * leg_ragged_create -- prepare the computation of `count` functions over the
+ * bucket plans plans[0..nplans-1] (all LEG_SPLIT_FP16, current device).
+ * Host arrays, copied:
+ *   plan_idx[i]  bucket of function i (0..nplans-1);
+ *   n_out[i]     coefficients kept for function i, 1..N of its plan;
+ *   in_off[i]    offset (in floats) of its K samples in the packed input;
+ *   out_off[i]   offset (in floats) of its n_out[i] coefficients in the
+ *                packed output.
+ * Allocates the per-bucket workspaces and a private stream; synchronises.
+ * The plans must outlive the batch.
+ *
+ * leg_forward_ragged -- Theorem 1 (Eq. 2.4, Eq. 2.5) for every function of
+ * the batch: one input-split launch over all functions, ONE persistent
+ * tcgen05 launch over the Abel-GEMM tiles of all buckets, one transform
+ * launch per bucket writing the packed output.  The first call runs the
+ * sequence directly; later calls replay it as a CUDA graph (captured again
+ * when f_packed or c_packed change).  Ordered after prior work on `stream`,
+ * and later work on `stream` waits for it.  Device pointers.
+ *
+ * leg_ragged_status -- as leg_plan_status, for the batch's kernels.
+ */
+typedef struct leg_ragged *leg_ragged_t;
+LEG_API int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int nplans, int count,
+                              const int *plan_idx, const int *n_out, const long long *in_off,
+                              const long long *out_off);
+LEG_API int leg_forward_ragged(leg_ragged_t batch, const float *f_packed, float *c_packed,
+                               cudaStream_t stream);
+LEG_API int leg_ragged_status(leg_ragged_t batch, int reset);
+LEG_API int leg_ragged_destroy(leg_ragged_t batch);
+
+/*
+ * leg_sample_cl -- input generation (no counterpart in the method): samples of
+ * closed-form functions at their Chebyshev-Lobatto nodes, evaluated in FP64 on
+ * the device and stored in FP32.  For function i with K[i] nodes,
+ *   f_packed[in_off[i] + k] = f_i(cos(pi k / (K[i]-1))),  k = 0..K[i]-1,
+ * family[i] = LEG_FAMILY_GENFN (param[i] = t), LEG_FAMILY_EXP (param[i] = a),
+ * or LEG_FAMILY_CHEB (sum_{m<K[i]} coef[coef_off[i] + m] T_m(x), by Clenshaw's
+ * recurrence; coef/coef_off may be NULL if no function uses this family).
+ * All arrays on the device.
+ */
+LEG_API int leg_sample_cl(int count, const int *family, const double *param, const int *K,
+                          const long long *coef_off, const double *coef, const long long *in_off,
+                          float *f_packed, cudaStream_t stream);
 
 /*
  * leg_plan_status -- synchronise with the device and report whether any
@@ -184,6 +232,24 @@ LEG_API int leg_plan_status(leg_plan_t plan, int reset);
 LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
 
 /*
+ * leg_plan_set_tile -- width of the output tile of the tensor-core Abel GEMM
+ * (LEG_SPLIT_FP16 forward and adjoint, LEG_BF16): tn functions per CTA-pair
+ * tile of 256 operator rows, a multiple of 16 in 16..256; 0 (the default)
+ * lets the library pick tn per call from the batch size, the rows and the
+ * number of resident CTA pairs (fewest MMA cycles on the busiest pair).
+ * A tuning knob only: results do not depend on it.
+ */
+LEG_API int leg_plan_set_tile(leg_plan_t plan, int tn);
+
+/*
+ * leg_plan_tile_info -- the tile of the forward GEMM for a batch of B
+ * functions: *tn functions per pair tile, *pairs CTA pairs resident at once
+ * on the current device, *tiles pair tiles of the launch.  LEG_SPLIT_FP16
+ * plans only (LEG_ERR_UNSUPPORTED otherwise).  Any output may be NULL.
+ */
+LEG_API int leg_plan_tile_info(leg_plan_t plan, int B, int *tn, int *pairs, int *tiles);
+
+/*
  * leg_forward_noalloc -- leg_forward for a LEG_SPLIT_FP16 plan that allocates
  * no device memory.  (The paper has no counterpart: this is a library
  * convenience.)  It is meant for callers that must not allocate at call time,
@@ -195,7 +261,7 @@ LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
  * The intermediate buffers (input slices, per-function scales, the Abel
  * GEMM result) come from one static device array of 64 MiB in the library,
  * which every GPU that loads the library keeps reserved until process exit.
- * A batch needing more scratch than that (about B*(6*Kp + 8*Mr) bytes, Kp = K
+ * A batch needing more scratch than that (about B*(10*Kp + 8*Mr) bytes, Kp = K
  * rounded up to 64, Mr = M/2+1 rounded up to 64) is rejected with
  * LEG_ERR_INVALID_ARG and a message stating the sizes.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that

@@ -21,13 +21,14 @@ import re
 import torch
 
 __all__ = [
-    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FAMILY_GENFN", "FAMILY_EXP",
+    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB",
+    "Ragged", "sample_cl",
     "LegError", "Plan", "LegendreFn", "legendre", "library_path", "declared_symbols", "load_library",
 ]
 
 F64, F32, BF16, SPLIT_FP16 = 0, 1, 2, 3
 FLAG_TAU_LITERAL = 1
-FAMILY_GENFN, FAMILY_EXP = 0, 1
+FAMILY_GENFN, FAMILY_EXP, FAMILY_CHEB = 0, 1, 2
 _ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -71,6 +72,13 @@ def _load():
         "leg_plain_forward": ([vp, i, vp, i, vp, vp], i),
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
+        "leg_plan_set_tile": ([vp, i], i),
+        "leg_plan_tile_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "leg_ragged_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i, i, vp, vp, vp, vp], i),
+        "leg_forward_ragged": ([vp, vp, vp, vp], i),
+        "leg_ragged_status": ([vp, i], i),
+        "leg_ragged_destroy": ([vp], i),
+        "leg_sample_cl": ([i, vp, vp, vp, vp, vp, vp, vp, vp], i),
         "leg_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -173,6 +181,17 @@ class Plan:
     def set_wait_limit(self, cycles: int):
         _check(_lib.leg_plan_set_wait_limit(self._h, int(cycles)))
 
+    def set_tile(self, tn: int):
+        """Functions per CTA-pair tile of the tensor-core GEMM (0 = automatic)."""
+        _check(_lib.leg_plan_set_tile(self._h, int(tn)))
+
+    def tile_info(self, B: int) -> dict:
+        """Tile of the split forward GEMM for B functions: tn, resident pairs, tiles."""
+        tn, pairs, tiles = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.leg_plan_tile_info(self._h, int(B), ctypes.byref(tn), ctypes.byref(pairs),
+                                       ctypes.byref(tiles)))
+        return {"tn": tn.value, "pairs": pairs.value, "tiles": tiles.value}
+
     def forward(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> torch.Tensor:
         """c = L f for f of shape (B, K) on the device (leg_forward)."""
         B = f.shape[0] if f.dim() == 2 else -1
@@ -243,3 +262,67 @@ class LegendreFn(torch.autograd.Function):
 def legendre(f: torch.Tensor, plan: Plan) -> torch.Tensor:
     """Differentiable Legendre coefficients of the rows of f (B x K CL samples)."""
     return LegendreFn.apply(f, plan)
+
+
+class Ragged:
+    """A ragged batch over size-bucket plans (leg_ragged_create / leg_forward_ragged).
+
+    plans: list of SPLIT_FP16 Plans; plan_idx, n_out, in_off, out_off: per
+    function (host sequences).  forward() reads the packed FP32 samples and
+    writes the packed coefficients (device tensors)."""
+
+    def __init__(self, plans, plan_idx, n_out, in_off, out_off):
+        import numpy as np
+        self.plans = list(plans)   # keep the plans alive
+        pi = np.ascontiguousarray(plan_idx, dtype=np.int32)
+        no = np.ascontiguousarray(n_out, dtype=np.int32)
+        io = np.ascontiguousarray(in_off, dtype=np.int64)
+        oo = np.ascontiguousarray(out_off, dtype=np.int64)
+        self.count = int(pi.size)
+        hp = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(_lib.leg_ragged_create(ctypes.byref(h), hp, len(self.plans), self.count,
+                                      pi.ctypes.data_as(ctypes.c_void_p), no.ctypes.data_as(ctypes.c_void_p),
+                                      io.ctypes.data_as(ctypes.c_void_p), oo.ctypes.data_as(ctypes.c_void_p)))
+        self._h = h
+        self.n_in = int((io + np.array([p.K for p in self.plans])[pi]).max()) if self.count else 0
+        self.n_out = int((oo + no).max()) if self.count else 0
+
+    def forward(self, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None) -> torch.Tensor:
+        for t, nm, n in ((f_packed, "f_packed", self.n_in), (c_packed, "c_packed", self.n_out)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("%s must be a contiguous float32 CUDA tensor" % nm)
+            if t.numel() < n:
+                raise ValueError("%s needs at least %d elements" % (nm, n))
+        _check(_lib.leg_forward_ragged(self._h, ctypes.c_void_p(f_packed.data_ptr()),
+                                       ctypes.c_void_p(c_packed.data_ptr()), _stream(stream)))
+        return c_packed
+
+    def status(self, reset: bool = True):
+        _check(_lib.leg_ragged_status(self._h, int(bool(reset))))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.leg_ragged_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sample_cl(family, param, K, in_off, f_packed, coef=None, coef_off=None, stream=None):
+    """leg_sample_cl: closed-form functions sampled at their CL nodes on the device.
+
+    All arguments are CUDA tensors: family int32, param float64, K int32,
+    in_off int64, f_packed float32; coef float64 and coef_off int64 for
+    FAMILY_CHEB."""
+    n = family.numel()
+
+    def ptr(t):
+        return ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+    _check(_lib.leg_sample_cl(n, ptr(family), ptr(param), ptr(K), ptr(coef_off), ptr(coef), ptr(in_off),
+                              ptr(f_packed), _stream(stream)))
+    return f_packed

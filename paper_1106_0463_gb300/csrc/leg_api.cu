@@ -16,10 +16,8 @@ void free_workspace(leg_plan *p)
 {
     cudaFree(p->G);
     cudaFree(p->Gbar);
-    for (int s = 0; s < 3; ++s) {
-        cudaFree(p->Fh[s]);
-        p->Fh[s] = nullptr;
-    }
+    cudaFree(p->Fh);
+    p->Fh = nullptr;
     cudaFree(p->Fbf);
     cudaFree(p->fexp);
     p->G = p->Gbar = nullptr;
@@ -36,8 +34,8 @@ void free_plan(leg_plan *p)
     cudaFree(p->wq);
     cudaFree(p->A64);
     cudaFree(p->A32);
-    for (int s = 0; s < 3; ++s) cudaFree(p->Ah[s]);
-    for (int s = 0; s < 3; ++s) cudaFree(p->AhT[s]);
+    cudaFree(p->Ah[0]);    // the three planes share one allocation
+    cudaFree(p->AhT[0]);
     cudaFree(p->Abf);
     cudaFree(p->rowexp);
     cudaFree(p->colexp);
@@ -70,8 +68,8 @@ int ensure_workspace(leg_plan *p, int B)
     LEG_CUDA_TRY(cudaMalloc(&p->Gbar, eb * Bz * p->ldg));
     if (p->dtype == LEG_SPLIT_FP16) {
         // input planes serve both directions: B x Kp (forward) or B x bwdKp (adjoint)
-        size_t w = (size_t)((p->Kp > bwdKp) ? p->Kp : bwdKp);
-        for (int s = 0; s < 3; ++s) LEG_CUDA_TRY(cudaMalloc(&p->Fh[s], sizeof(__half) * Bz * w));
+        p->ldf = (p->Kp > bwdKp) ? p->Kp : bwdKp;
+        LEG_CUDA_TRY(cudaMalloc(&p->Fh, sizeof(__half) * LEG_SPLIT_NF * Bz * p->ldf));
         LEG_CUDA_TRY(cudaMalloc(&p->fexp, sizeof(int) * Bz));
     } else if (p->dtype == LEG_BF16) {
         LEG_CUDA_TRY(cudaMalloc(&p->Fbf, sizeof(__nv_bfloat16) * Bz * p->Kp));
@@ -358,5 +356,30 @@ extern "C" int leg_plan_set_wait_limit(leg_plan_t p, long long cycles)
     if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
     if (cycles < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "cycles < 0");
     p->wait_limit = cycles;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (tn != 0 && (tn < 16 || tn > 256 || tn % 16 != 0))
+        return leg_set_error(LEG_ERR_INVALID_ARG, "tile width must be 0 or a multiple of 16 in 16..256");
+    p->tn = tn;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_tile_info(leg_plan_t p, int B, int *tn, int *pairs, int *tiles)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (p->dtype != LEG_SPLIT_FP16)
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "tile information is for LEG_SPLIT_FP16 plans");
+    if (B < 1) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 1");
+    int np = 0;
+    if ((rc = leg_split_max_pairs(&np))) return rc;
+    const int t = leg_split_choose_tn(p, B);
+    if (tn) *tn = t;
+    if (pairs) *pairs = np;
+    if (tiles) *tiles = ((p->rows - 1 + 255) / 256) * ((B + t - 1) / t);
     return LEG_OK;
 }

@@ -1,0 +1,581 @@
+// Register-tiled real-even transform for the FFT stage (FP64 and double-float).
+//
+// Same mathematics as the half-length transform in leg_fft.cu (arXiv:1106.0463,
+// Theorem 1: Eq. 2.4 with the twist of Eq. 2.5 as a first difference, the
+// symmetry Eq. 2.12 folding the M-point real-even sequence to L + 1 = M/2 + 1
+// values, and c_n = (2n+1) a_n):
+//   y_j = (x_j + x_{L-j})/2 - sin(pi j/L)(x_j - x_{L-j}),  0 <= j < L,
+//   z_m = y_{2m} + i y_{2m+1},  Z = FFT_H(z)  (H = L/2, positive exponent),
+//   2 Y_k = (Z_k + conj Z_{H-k}) + e^{2 pi i k/L}(...)  (real-data recombination),
+//   X_{2k} = 2 Re Y_k,  X_{2k+1} = X_1 + sum_{k'=1..k} 2 Im Y_{k'},
+//   X_1 = x_0 - x_L + 2 sum_{j=1}^{L/2-1} (x_j - x_{L-j}) cos(pi j/L),
+// so that X_n = sum_{j<M} g_j cos(2 pi n j/M) for n = 0..L.
+//
+// Layout: a function's H complex values live in registers, E = min(16, H/32)
+// per thread, T = H/E threads per function (one warp for H = 512).  The FFT
+// is a Stockham autosort of radix-E passes (the last pass takes the remaining
+// power of two): each thread holds x[t + b T], b < E, forms E/R radix-R
+// butterflies from them, applies the inter-pass twiddles (M-th roots of unity
+// from the FP64-built table), transforms in registers (a radix-2 network with
+// constant twiddles) and writes the outputs to their autosorted positions in
+// shared memory, padded by one slot per 16 to avoid bank conflicts.  The fold
+// is computed while the first pass reads G, the prefix of Im Y by warp
+// shuffles.  Double-float sums and products inside a pass skip the final
+// renormalisation (the error terms stay exact: TwoSum and FMA products); values
+// are renormalised when stored.  Functions of T = 32 synchronise with
+// __syncwarp only.
+#include "leg_fft.cuh"
+#include "leg_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- arithmetic
+template <class T> struct Fa;
+
+template <> struct Fa<double> {
+    using T = double;
+    static __device__ __forceinline__ T add(T a, T b) { return a + b; }
+    static __device__ __forceinline__ T sub(T a, T b) { return a - b; }
+    static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+    static __device__ __forceinline__ T neg(T a) { return -a; }
+    static __device__ __forceinline__ T half(T a) { return 0.5 * a; }
+    static __device__ __forceinline__ T norm(T a) { return a; }
+    static __device__ __forceinline__ T cst(double v) { return v; }
+    static __device__ __forceinline__ T zero() { return 0.0; }
+    static __device__ __forceinline__ T pow2(T a, int e) { return ldexp(a, e); }
+};
+
+template <> struct Fa<dfl> {
+    using T = dfl;
+    // TwoSum of the leading parts, trailing parts added without renormalising
+    static __device__ __forceinline__ T add(T a, T b)
+    {
+        const float s = a.hi + b.hi;
+        const float bb = s - a.hi;
+        const float e = (a.hi - (s - bb)) + (b.hi - bb);
+        return {s, e + (a.lo + b.lo)};
+    }
+    static __device__ __forceinline__ T neg(T a) { return {-a.hi, -a.lo}; }
+    static __device__ __forceinline__ T sub(T a, T b) { return add(a, neg(b)); }
+    // exact product of the leading parts (FMA), cross terms added, no renormalisation
+    static __device__ __forceinline__ T mul(T a, T b)
+    {
+        const float p = a.hi * b.hi;
+        float e = fmaf(a.hi, b.hi, -p);
+        e = fmaf(a.hi, b.lo, e);
+        e = fmaf(a.lo, b.hi, e);
+        return {p, e};
+    }
+    static __device__ __forceinline__ T half(T a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+    static __device__ __forceinline__ T norm(T a)
+    {
+        const float s = a.hi + a.lo;
+        return {s, a.lo - (s - a.hi)};
+    }
+    static __device__ __forceinline__ T cst(double v)
+    {
+        const float h = (float)v;
+        return {h, (float)(v - (double)h)};
+    }
+    static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
+    static __device__ __forceinline__ T pow2(T a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
+};
+
+template <class R> using CxT = Cx<typename Fa<R>::T>;
+
+template <class R>
+__device__ __forceinline__ CxT<R> cadd(CxT<R> a, CxT<R> b)
+{
+    using F = Fa<R>;
+    return {F::add(a.re, b.re), F::add(a.im, b.im)};
+}
+
+template <class R>
+__device__ __forceinline__ CxT<R> csub(CxT<R> a, CxT<R> b)
+{
+    using F = Fa<R>;
+    return {F::sub(a.re, b.re), F::sub(a.im, b.im)};
+}
+
+template <class R>
+__device__ __forceinline__ CxT<R> cmul(CxT<R> a, typename Fa<R>::T c, typename Fa<R>::T s)
+{
+    using F = Fa<R>;
+    return {F::sub(F::mul(a.re, c), F::mul(a.im, s)), F::add(F::mul(a.re, s), F::mul(a.im, c))};
+}
+
+// a * e^{2 pi i m / 16}, m = 0..7 (constant)
+template <class R, int m>
+__device__ __forceinline__ CxT<R> wmul16(CxT<R> a)
+{
+    using F = Fa<R>;
+    constexpr double C1 = 0.92387953251128675613, S1 = 0.38268343236508977173, H2 = 0.70710678118654752440;
+    if constexpr (m == 0) {
+        return a;
+    } else if constexpr (m == 4) {
+        return {F::neg(a.im), a.re};
+    } else if constexpr (m == 2) {
+        const auto h = F::cst(H2);
+        return {F::mul(h, F::sub(a.re, a.im)), F::mul(h, F::add(a.re, a.im))};
+    } else if constexpr (m == 6) {
+        const auto h = F::cst(H2);
+        return {F::neg(F::mul(h, F::add(a.re, a.im))), F::mul(h, F::sub(a.re, a.im))};
+    } else {
+        constexpr double c = (m == 1) ? C1 : (m == 3) ? S1 : (m == 5) ? -S1 : -C1;
+        constexpr double s = (m == 1) ? S1 : (m == 3) ? C1 : (m == 5) ? C1 : S1;
+        return cmul<R>(a, F::cst(c), F::cst(s));
+    }
+}
+
+__host__ __device__ constexpr int bitrev(int n, int bits)
+{
+    int r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((n >> i) & 1) << (bits - 1 - i);
+    return r;
+}
+
+// Butterflies m..S-1 of a radix-2 stage (half-size S) on the block at blk:
+// twiddle e^{2 pi i m / (2S)} = W16^{m * 16 / (2S)}.
+template <class R, int P, int S, int m>
+struct Bfly {
+    static __device__ __forceinline__ void run(CxT<R> (&x)[P], int blk)
+    {
+        if constexpr (m < S) {
+            const CxT<R> b = wmul16<R, m * (16 / (2 * S))>(x[blk + m + S]);
+            const CxT<R> a = x[blk + m];
+            x[blk + m] = cadd<R>(a, b);
+            x[blk + m + S] = csub<R>(a, b);
+            Bfly<R, P, S, m + 1>::run(x, blk);
+        }
+    }
+};
+
+template <class R, int P, int S>
+__device__ __forceinline__ void dft_stage(CxT<R> (&x)[P])
+{
+    if constexpr (S < P) {
+#pragma unroll
+        for (int blk = 0; blk < P; blk += 2 * S) Bfly<R, P, S, 0>::run(x, blk);
+        dft_stage<R, P, 2 * S>(x);
+    }
+}
+
+// In-register DFT of size P (2, 4, 8 or 16), positive exponent, natural order
+// in and out: radix-2 decimation in time on the bit-reversed inputs.
+template <class R, int P, int LOGP>
+__device__ __forceinline__ void dft(CxT<R> (&x)[P])
+{
+    CxT<R> y[P];
+#pragma unroll
+    for (int i = 0; i < P; ++i) y[i] = x[bitrev(i, LOGP)];
+#pragma unroll
+    for (int i = 0; i < P; ++i) x[i] = y[i];
+    dft_stage<R, P, 1>(x);
+}
+
+#ifndef LEG_DCT16_LOG2E
+#define LEG_DCT16_LOG2E 3   // at most 2^LEG_DCT16_LOG2E complex values per thread
+#endif
+
+template <int LOG2H> struct D16 {
+    static constexpr int H = 1 << LOG2H;
+    static constexpr int L = 2 * H;
+    static constexpr int M = 2 * L;
+    static constexpr int LOG2E = (LOG2H - 5 < LEG_DCT16_LOG2E) ? LOG2H - 5 : LEG_DCT16_LOG2E;
+    static constexpr int E = 1 << LOG2E;
+    static constexpr int T = H / E;                                 // threads per function, >= 32
+    static constexpr int FPB = (T >= 128) ? 1 : 128 / T;            // functions per CTA
+    static constexpr int THREADS = T * FPB;
+    static constexpr int SLOTS = H + H / E + 1;                     // padded complex slots per function
+    static constexpr int WARPS = T / 32;
+    // FFT buffer: one padding slot per E complex values; real view (X): one
+    // padding word per 2E words.  Both keep a warp's accesses conflict-free
+    // for consecutive and for E-strided indices.
+    static __device__ __forceinline__ int pc(int i) { return i + (i >> LOG2E); }
+    static __device__ __forceinline__ int px(int i) { return i + (i >> (LOG2E + 1)); }
+};
+
+template <int T>
+__device__ __forceinline__ void fsync()
+{
+    if constexpr (T == 32) __syncwarp();
+    else __syncthreads();
+}
+
+// Twiddle (cos, sin) of 2 pi i / M from the table (double2 or float4 double-float).
+__device__ __forceinline__ void twid(const double2 *tw, int i, double &c, double &s)
+{
+    const double2 v = tw[i];
+    c = v.x;
+    s = v.y;
+}
+__device__ __forceinline__ void twid(const float4 *tw, int i, dfl &c, dfl &s)
+{
+    const float4 v = tw[i];
+    c = {v.x, v.y};
+    s = {v.z, v.w};
+}
+
+// One Stockham pass of radix P over v = x[t + b T] (b < E): butterflies
+// j = t + bb T (bb < E/P) of stride Ns, twiddles e^{2 pi i r k / (P Ns)},
+// outputs to buf[D::pc((j - k) P + k + r Ns)].
+template <class R, int LOG2H, int P, int LOGP>
+__device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, int t, int Ns,
+                                         const typename Ar<R>::TW *tw)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    constexpr int E = D::E, T = D::T, NB = E / P;
+    const int tstep = D::M / (P * Ns);
+#pragma unroll
+    for (int bb = 0; bb < NB; ++bb) {
+        const int j = t + bb * T;
+        const int k = j & (Ns - 1);
+        CxT<R> x[P];
+#pragma unroll
+        for (int r = 0; r < P; ++r) x[r] = v[bb + r * NB];
+        if (k != 0) {
+#pragma unroll
+            for (int r = 1; r < P; ++r) {
+                typename F::T c, s;
+                twid(tw, r * k * tstep, c, s);
+                x[r] = cmul<R>(x[r], c, s);
+            }
+        }
+        dft<R, P, LOGP>(x);
+        const int o = (j - k) * P + k;
+#pragma unroll
+        for (int r = 0; r < P; ++r) {
+            CxT<R> y = {F::norm(x[r].re), F::norm(x[r].im)};
+            buf[D::pc(o + r * Ns)] = y;
+        }
+    }
+}
+
+template <class R, int LOG2H>
+__device__ __forceinline__ void fft_pass_any(int P, CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, int t, int Ns,
+                                             const typename Ar<R>::TW *tw)
+{
+    if constexpr (D16<LOG2H>::E >= 16) {
+        if (P == 16) return fft_pass<R, LOG2H, 16, 4>(v, buf, t, Ns, tw);
+    }
+    if constexpr (D16<LOG2H>::E >= 8) {
+        if (P == 8) return fft_pass<R, LOG2H, 8, 3>(v, buf, t, Ns, tw);
+    }
+    if constexpr (D16<LOG2H>::E >= 4) {
+        if (P == 4) return fft_pass<R, LOG2H, 4, 2>(v, buf, t, Ns, tw);
+    }
+    fft_pass<R, LOG2H, 2, 1>(v, buf, t, Ns, tw);
+}
+
+__device__ __forceinline__ double shfl_up(double v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ dfl shfl_up(dfl v, int off)
+{
+    return {__shfl_up_sync(0xffffffffu, v.hi, off), __shfl_up_sync(0xffffffffu, v.lo, off)};
+}
+__device__ __forceinline__ double shfl_xor(double v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+__device__ __forceinline__ dfl shfl_xor(dfl v, int off)
+{
+    return {__shfl_xor_sync(0xffffffffu, v.hi, off), __shfl_xor_sync(0xffffffffu, v.lo, off)};
+}
+
+// Inclusive scan of v over the T threads of a function (warp shuffles, then
+// the warp totals through shared memory).  wsum: D::WARPS slots per function.
+template <class R, int LOG2H>
+__device__ __forceinline__ typename Fa<R>::T fn_scan(typename Fa<R>::T v, int t, typename Fa<R>::T *wsum)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    const int lane = t & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T_ u = shfl_up(v, off);
+        if (lane >= off) v = F::add(v, u);
+    }
+    if constexpr (D::WARPS > 1) {
+        const int w = t >> 5;
+        if (lane == 31) wsum[w] = v;
+        __syncthreads();
+        T_ before = F::zero();
+        for (int i = 0; i < w; ++i) before = F::add(before, wsum[i]);
+        v = F::add(before, v);
+        __syncthreads();
+    }
+    return v;
+}
+
+// Sum of v over the T threads of a function, returned to every thread.
+template <class R, int LOG2H>
+__device__ __forceinline__ typename Fa<R>::T fn_sum(typename Fa<R>::T v, int t, typename Fa<R>::T *wsum)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v = F::add(v, shfl_xor(v, off));
+    if constexpr (D::WARPS > 1) {
+        if ((t & 31) == 0) wsum[t >> 5] = v;
+        __syncthreads();
+        v = wsum[0];
+        for (int i = 1; i < D::WARPS; ++i) v = F::add(v, wsum[i]);
+        __syncthreads();
+    }
+    return v;
+}
+
+// X_0..X_L of the L+1 values delivered by load(j) (the caller's element type
+// converted to the arithmetic type), left in Xs[D::px(n)], n = 0..L (a real
+// view of buf).
+template <class R, int LOG2H, class Load>
+__device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int t, const typename Ar<R>::TW *tw,
+                                      Load load)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
+    CxT<R> v[E];
+
+    // 1. fold into z_m = y_{2m} + i y_{2m+1} for m = t + b T; partial X_1 sum
+    T_ part = F::zero();
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+        const int m = t + b * T;
+        T_ yy[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int j = 2 * m + u;
+            const T_ xj = load(j), xl = load(L - j);
+            T_ c, s;
+            twid(tw, j, c, s);                 // cos, sin of pi j / L
+            const T_ d = F::sub(xj, xl);
+            yy[u] = F::sub(F::half(F::add(xj, xl)), F::mul(s, d));
+            if (j >= 1 && j < L / 2) part = F::add(part, F::mul(c, d));
+        }
+        v[b] = {F::norm(yy[0]), F::norm(yy[1])};
+    }
+    const T_ x1 = F::norm(F::add(F::sub(load(0), load(L)), F::pow2(fn_sum<R, LOG2H>(part, t, wsum), 1)));
+
+    // 2. FFT of length H: Stockham passes of radix E (the last one smaller)
+    int Ns = 1;
+    {
+        constexpr int P0 = (E < H) ? E : H;
+        fft_pass_any<R, LOG2H>(P0, v, buf, t, 1, tw);
+        Ns = P0;
+    }
+    while (Ns < H) {
+        fsync<T>();
+#pragma unroll
+        for (int b = 0; b < E; ++b) v[b] = buf[D::pc(t + b * T)];
+        fsync<T>();
+        const int P = (H / Ns < E) ? H / Ns : E;
+        fft_pass_any<R, LOG2H>(P, v, buf, t, Ns, tw);
+        Ns *= P;
+    }
+    fsync<T>();
+
+    // 3. recombination for k = t + i T: 2 Re Y_k (= X_2k) and 2 Im Y_k
+    T_ ry[E], iy[E];
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = t + i * T;
+        const CxT<R> za = buf[D::pc(k)], zb = buf[D::pc((H - k) & (H - 1))];
+        T_ c, s;
+        twid(tw, 2 * k, c, s);                 // e^{2 pi i k / L}
+        const T_ sre = F::add(za.re, zb.re), dre = F::sub(za.re, zb.re);
+        const T_ sim = F::add(za.im, zb.im), dim = F::sub(za.im, zb.im);
+        ry[i] = F::norm(F::add(sre, F::add(F::mul(c, sim), F::mul(s, dre))));
+        iy[i] = (k == 0) ? F::zero() : F::norm(F::add(dim, F::sub(F::mul(s, sim), F::mul(c, dre))));
+    }
+    T_ xL = F::zero();
+    if (t == T - 1) {
+        const CxT<R> z0 = buf[D::pc(0)];
+        xL = F::norm(F::pow2(F::sub(z0.re, z0.im), 1));   // X_L = 2 Re Y_H
+    }
+    fsync<T>();
+    // 4. X_2k in place; 2 Im Y_k parked in the odd slots
+    T_ *Xs = reinterpret_cast<T_ *>(buf);
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        const int k = t + i * T;
+        Xs[D::px(2 * k)] = ry[i];
+        Xs[D::px(2 * k + 1)] = iy[i];
+    }
+    if (t == T - 1) Xs[D::px(L)] = xL;
+    fsync<T>();
+    // 5. X_{2k+1} = X_1 + sum_{k' <= k} 2 Im Y_k': each thread scans k = t E .. t E + E - 1
+    T_ run = F::zero();
+#pragma unroll
+    for (int i = 0; i < E; ++i) {
+        run = F::add(run, Xs[D::px(2 * (t * E + i) + 1)]);
+        iy[i] = run;
+    }
+    const T_ incl = fn_scan<R, LOG2H>(run, t, wsum);
+    const T_ offs = F::add(x1, F::sub(incl, run));   // X_1 + exclusive prefix
+#pragma unroll
+    for (int i = 0; i < E; ++i) Xs[D::px(2 * (t * E + i) + 1)] = F::norm(F::add(offs, iy[i]));
+    fsync<T>();
+}
+
+template <class R> struct GIn;
+template <> struct GIn<double> {
+    static __device__ __forceinline__ double get(const double *g, int j) { return g[j]; }
+};
+template <> struct GIn<dfl> {
+    static __device__ __forceinline__ dfl get(const float2 *g, int j)
+    {
+        const float2 v = g[j];
+        return {v.x, v.y};
+    }
+};
+
+__device__ __forceinline__ double out_of(double a) { return a; }
+__device__ __forceinline__ float out_of(dfl a) { return a.hi + a.lo; }
+
+// c[f, n] = (2n+1)(X_n - X_{n+1}) / M, n < N (or, with rowfn, the first
+// n_out coefficients of function rowfn[f] at c + out_off[.]).
+template <class R, int LOG2H>
+__global__ void __launch_bounds__(D16<LOG2H>::THREADS) dct16_forward_kernel(
+    const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
+    const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
+    const int *__restrict__ n_out)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
+    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * D::SLOTS) + grp * D::WARPS;
+    const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
+    const bool live = blockIdx.x * D::FPB + grp < B;
+    const typename Ar<R>::GT *g = G + (size_t)f * ldg;
+    dct16<R, LOG2H>(buf, wsum, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
+    if (!live) return;
+    const T_ *Xs = reinterpret_cast<const T_ *>(buf);
+    typename Ar<R>::OUT *cf = c + (size_t)f * N;
+    int nn = N;
+    if (rowfn) {
+        const int fg = rowfn[f];
+        cf = c + out_off[fg];
+        nn = min(N, n_out[fg]);
+    }
+    constexpr int SHIFT = -(LOG2H + 2);   // 1 / M
+    for (int n = t; n < nn; n += D::T) {
+        const T_ a = F::pow2(F::sub(Xs[D::px(n)], Xs[D::px(n + 1)]), SHIFT);
+        cf[n] = out_of(F::norm(F::mul(F::cst((double)(2 * n + 1)), a)));
+    }
+}
+
+// gbar[f, j] = (w_j / 2M)(X_j + x_0 + (-1)^j x_L), j = 0..L, for
+// x_n = (2n+1) v_n - (2n-1) v_{n-1} (n <= N, zero beyond).
+template <class R, class VIN, int LOG2H>
+__global__ void __launch_bounds__(D16<LOG2H>::THREADS) dct16_adjoint_kernel(
+    const VIN *__restrict__ v, typename Ar<R>::GT *__restrict__ gbar, int ldg, int N, int B,
+    const typename Ar<R>::TW *__restrict__ tw)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    constexpr int L = D::L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
+    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * D::SLOTS) + grp * D::WARPS;
+    const int f = min(blockIdx.x * D::FPB + grp, B - 1);
+    const bool live = blockIdx.x * D::FPB + grp < B;
+    const VIN *vf = v + (size_t)f * N;
+    auto load = [&](int n) -> T_ {
+        if (n > N) return F::zero();
+        T_ x = F::zero();
+        if (n < N) x = F::mul(F::cst((double)(2 * n + 1)), F::cst((double)vf[n]));
+        if (n >= 1) x = F::sub(x, F::mul(F::cst((double)(2 * n - 1)), F::cst((double)vf[n - 1])));
+        return x;
+    };
+    dct16<R, LOG2H>(buf, wsum, t, tw, load);
+    if (!live) return;
+    const T_ *Xs = reinterpret_cast<const T_ *>(buf);
+    const T_ x0 = load(0), xL = load(L);
+    for (int j = t; j <= L; j += D::T) {
+        const T_ s = F::add(Xs[D::px(j)], F::add(x0, (j & 1) ? F::neg(xL) : xL));
+        const int e = (j == 0 || j == L) ? -(LOG2H + 3) : -(LOG2H + 2);
+        gbar[(size_t)f * ldg + j] = Ar<R>::to_g(F::norm(F::pow2(s, e)));
+    }
+}
+
+template <class R, int LOG2H>
+size_t d16_smem()
+{
+    using D = D16<LOG2H>;
+    return sizeof(CxT<R>) * D::FPB * D::SLOTS + sizeof(typename Fa<R>::T) * D::FPB * D::WARPS;
+}
+
+template <class R, int LOG2H>
+int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
+               const long long *out_off, const int *n_out)
+{
+    using D = D16<LOG2H>;
+    auto kern = dct16_forward_kernel<R, LOG2H>;
+    const size_t smem = d16_smem<R, LOG2H>();
+    LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (B + D::FPB - 1) / D::FPB;
+    kern<<<grid, D::THREADS, smem, st>>>(static_cast<const typename Ar<R>::GT *>(G), ldg,
+                                         static_cast<typename Ar<R>::OUT *>(c), N, B,
+                                         static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out);
+    LEG_LAUNCH_CHECK("dct16_forward_kernel");
+    return LEG_OK;
+}
+
+template <class R, class VIN, int LOG2H>
+int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+{
+    using D = D16<LOG2H>;
+    auto kern = dct16_adjoint_kernel<R, VIN, LOG2H>;
+    const size_t smem = d16_smem<R, LOG2H>();
+    LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (B + D::FPB - 1) / D::FPB;
+    kern<<<grid, D::THREADS, smem, st>>>(static_cast<const VIN *>(v), static_cast<typename Ar<R>::GT *>(gbar), ldg,
+                                         N, B, static_cast<const typename Ar<R>::TW *>(tw));
+    LEG_LAUNCH_CHECK("dct16_adjoint_kernel");
+    return LEG_OK;
+}
+
+template <class R, int LO, int HI>
+int dispatch_fwd(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+                 const int *rowfn, const long long *out_off, const int *n_out)
+{
+    if constexpr (LO > HI) {
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
+    } else {
+        if (lg == LO) return launch_fwd<R, LO>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        return dispatch_fwd<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    }
+}
+
+template <class R, class VIN, int LO, int HI>
+int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+{
+    if constexpr (LO > HI) {
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
+    } else {
+        if (lg == LO) return launch_adj<R, VIN, LO>(v, gbar, ldg, N, B, tw, st);
+        return dispatch_adj<R, VIN, LO + 1, HI>(lg, v, gbar, ldg, N, B, tw, st);
+    }
+}
+
+}  // namespace
+
+// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768).
+int leg_dct16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
+                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
+{
+    if (dtype == LEG_F64) return dispatch_fwd<double, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    return dispatch_fwd<dfl, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+}
+
+int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
+                      cudaStream_t st)
+{
+    if (dtype == LEG_F64) return dispatch_adj<double, double, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
+    return dispatch_adj<dfl, float, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
+}

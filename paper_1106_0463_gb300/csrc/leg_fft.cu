@@ -370,10 +370,14 @@ __device__ void dct1_half(Cx<typename Ar<R>::T> *buf, typename Ar<R>::T *red, ty
     __syncthreads();
 }
 
+// rowfn == nullptr: c is B x N row-major.  Otherwise (ragged batches) row f of
+// G belongs to function rowfn[f], whose first n_out[.] coefficients go to
+// c + out_off[.].
 template <class R, int LOG2H>
 __global__ void __launch_bounds__(DctShape<LOG2H>::THREADS) dct_forward_kernel(
     const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c,
-    int N, int B, const typename Ar<R>::TW *__restrict__ tw)
+    int N, int B, const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn,
+    const long long *__restrict__ out_off, const int *__restrict__ n_out)
 {
     using A = Ar<R>;
     using T = typename A::T;
@@ -393,9 +397,16 @@ __global__ void __launch_bounds__(DctShape<LOG2H>::THREADS) dct_forward_kernel(
     if (!live) return;
     const T *Xs = reinterpret_cast<const T *>(buf);
     constexpr int SHIFT = -(LOG2H + 2);   // 1 / M
-    for (int n = t; n < N; n += D::TPF) {
+    typename A::OUT *cf = c + (size_t)f * N;
+    int nn = N;
+    if (rowfn) {
+        const int fg = rowfn[f];
+        cf = c + out_off[fg];
+        nn = min(N, n_out[fg]);
+    }
+    for (int n = t; n < nn; n += D::TPF) {
         T a = A::pow2(A::sub(Xs[n], Xs[n + 1]), SHIFT);
-        c[(size_t)f * N + n] = A::out(A::mul(A::from_int(2 * n + 1), a));
+        cf[n] = A::out(A::mul(A::from_int(2 * n + 1), a));
     }
 }
 
@@ -438,7 +449,8 @@ __global__ void __launch_bounds__(DctShape<LOG2H>::THREADS) dct_adjoint_kernel(
 }
 
 template <class R, int LOG2H>
-int launch_dct_forward(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st)
+int launch_dct_forward(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+                       const int *rowfn = nullptr, const long long *out_off = nullptr, const int *n_out = nullptr)
 {
     using A = Ar<R>;
     using D = DctShape<LOG2H>;
@@ -448,7 +460,7 @@ int launch_dct_forward(const void *G, int ldg, void *c, int N, int B, const void
     int grid = (B + D::FPB - 1) / D::FPB;
     kern<<<grid, D::THREADS, smem, st>>>(static_cast<const typename A::GT *>(G), ldg,
                                          static_cast<typename A::OUT *>(c), N, B,
-                                         static_cast<const typename A::TW *>(tw));
+                                         static_cast<const typename A::TW *>(tw), rowfn, out_off, n_out);
     LEG_LAUNCH_CHECK("dct_forward_kernel");
     return LEG_OK;
 }
@@ -470,13 +482,15 @@ int launch_dct_adjoint(const void *v, void *gbar, int ldg, int N, int B, const v
 }
 
 template <class R, int LO, int HI>
-int dispatch_dct_forward(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st)
+int dispatch_dct_forward(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+                         const int *rowfn = nullptr, const long long *out_off = nullptr,
+                         const int *n_out = nullptr)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length not supported");
     } else {
-        if (lg == LO) return launch_dct_forward<R, LO>(G, ldg, c, N, B, tw, st);
-        return dispatch_dct_forward<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st);
+        if (lg == LO) return launch_dct_forward<R, LO>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        return dispatch_dct_forward<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }
 
@@ -555,17 +569,27 @@ int ilog2(int x)
 
 }  // namespace
 
+// The FP64 and double-float transforms take the register-tiled kernels of
+// leg_dct16.cu from H = L/2 = 64 up (M >= 256), the shared-memory Stockham
+// kernels above below that.
+constexpr int DCT16_MIN_LOG2H = 6;
+
 int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, cudaStream_t st)
 {
     if (B == 0) return LEG_OK;
     const int lg = ilog2(p->L);
     switch (p->dtype) {
     case LEG_F64:
+        if (lg - 1 >= DCT16_MIN_LOG2H)
+            return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
         return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
         return dispatch_forward<float, 2, 14>(lg, G, ldg, c, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
+        if (lg - 1 >= DCT16_MIN_LOG2H)
+            return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c, p->N, B, p->twdf, st, nullptr, nullptr,
+                                     nullptr);
         return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->twdf, st);
     }
     return leg_set_error(LEG_ERR_INVALID_ARG, "bad dtype");
@@ -577,11 +601,14 @@ int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B
     const int lg = ilog2(p->L);
     switch (p->dtype) {
     case LEG_F64:
+        if (lg - 1 >= DCT16_MIN_LOG2H) return leg_dct16_adjoint(LEG_F64, lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
         return dispatch_dct_adjoint<double, double, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
         return dispatch_adjoint<float, float, 2, 14>(lg, v, gbar, ldg, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
+        if (lg - 1 >= DCT16_MIN_LOG2H)
+            return leg_dct16_adjoint(LEG_SPLIT_FP16, lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
         return dispatch_dct_adjoint<dfl, float, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
     }
     return leg_set_error(LEG_ERR_INVALID_ARG, "bad dtype");
@@ -591,5 +618,22 @@ int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B
 int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, int B, cudaStream_t st)
 {
     if (B == 0) return LEG_OK;
-    return dispatch_dct_forward<double, 1, 13>(ilog2(p->L) - 1, G, ldg, c, p->N, B, p->tw64, st);
+    const int lg = ilog2(p->L);
+    if (lg - 1 >= DCT16_MIN_LOG2H)
+        return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
+    return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
+}
+
+// Ragged batches: the rows of G (double-float) scatter their first n_out
+// coefficients into the packed output.
+int leg_fft_forward_ragged(const leg_plan *p, const void *G, int ldg, float *c_packed, int B, const int *rowfn,
+                           const long long *out_off, const int *n_out, cudaStream_t st)
+{
+    if (B == 0) return LEG_OK;
+    if (p->dtype != LEG_SPLIT_FP16) return leg_set_error(LEG_ERR_UNSUPPORTED, "ragged batches need split plans");
+    const int lg = ilog2(p->L);
+    if (lg - 1 >= DCT16_MIN_LOG2H)
+        return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off,
+                                 n_out);
+    return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off, n_out);
 }

@@ -2,41 +2,62 @@
 //
 // The Abel step of the method (arXiv:1106.0463, Eq. 2.5 evaluated by the
 // quadrature of Sec. 2 after Eq. 2.14) is, for a batch of sampled functions,
-// the dense product  G[b, j] = sum_k F[b, k] A[j, k]  (rows j = 0..M/2 of the
+// the dense product  G[b, j] = sum_k A[j, k] F[b, k]  (rows j = 0..M/2 of the
 // grid y_j = 2 pi j/M, K Chebyshev-Lobatto samples).  Its result is
 // differenced and scaled by (2n+1) in the FFT stage, which turns white
 // rounding noise in G into errors ~ (2N/sqrt(M)) times larger in c_n; FP32
 // accumulation of the whole product therefore cannot meet 1e-6.
 //
-// LEG_SPLIT_FP16 (three-slice split, eight products, four accumulators):
+// LEG_SPLIT_FP16 (three-slice split, six products, two accumulators):
 //   each operand row is scaled by a power of two (the operator by its L1
-//   norm, the input by its max-norm) and split into FP16 slices
-//     a = A0 + 2^-7 A1 + 2^-14 A2s,   f = F0 + 2^-7 F1 + 2^-14 F2s,
-//   where A0 lies on a 2^-16 grid and F0 on a 2^-7 grid.  Every product
-//   A0*F0 is then a multiple of 2^-23 and every partial sum of them is below
-//   2 in magnitude, so accumulator 0 (A0 F0) is EXACT in FP32 whatever the
-//   accumulation order or truncation of the tensor core.  Accumulators 1-3
-//   hold the terms of weight 2^-7 (A1 F0 + A0 F1), 2^-14 (A1 F1 + A2s F0 +
-//   A0 F2s) and 2^-21 (A2s F1 + F2s A1); their FP32 rounding stays below the
-//   target, and only terms of weight 2^-28 (A2s F2s) are dropped.  The
-//   epilogue forms G = 2^(e_b + e_j) (acc0 + 2^-7 acc1 + 2^-14 acc2 +
-//   2^-21 acc3) as a double-float pair for the double-float FFT.
-// LEG_BF16: one BF16 product into one FP32 accumulator (FP32 G).
+//   norm, the input by its max-norm) and split into FP16 slices, s = 7:
+//     a = A0 + 2^-s A1 + 2^-2s A2s,     A0 on a 2^-16 grid,
+//     f = F0 + 2^-s r,  r = F1 + (r - F1),   F0 on a 2^-s grid.
+//   Accumulator 0 takes A0 F0: the products lie on a 2^-23 grid and every
+//   partial sum stays below 2, so it is EXACT in FP32 whatever the order or
+//   truncation of the tensor core's additions.  Accumulator 1 (weight 2^-s)
+//   takes A1 F0 + A0 F1 + A0 (r - F1) + A1 (2^-s F1) + A2s (2^-s F0): the
+//   terms of weight 2^-2s reach it through input planes pre-scaled by 2^-s
+//   (exact for F0; below the FP16 normal range for F1 and r - F1 they keep an
+//   absolute 2^-25, which the L1-normalised rows bound by 2^-32 in G).  The
+//   dropped terms A2s F1, A1 (r - F1) and A2s (r - F1) have weight <= 2^-3s
+//   times slices below 2^-10.
+//   Accumulator 0 runs over the whole K range of a tile (it is exact).
+//   Accumulator 1 is split into chunks of 256 K: after each chunk the
+//   epilogue warps add it into registers and release its TMEM buffer, which
+//   bounds the tensor core's truncation error of accumulator 1 (it grows
+//   with the chunk's length and magnitude).  The epilogue forms
+//   G = 2^(e_j + e_b) (acc0 + 2^-s acc1) as a double-float pair.
+// LEG_BF16: one BF16 product, one accumulator (FP32 G).
 //
-// Kernel structure (one 128 x 128 output tile per CTA, 320 threads):
-//   warp 0 lane 0  TMA producer: per 32-wide K block, loads the operand tiles
-//                  (128 rows x 32 FP16, 64-byte swizzle) into one of four
-//                  stages and arms the stage's full barrier with the byte count;
-//   warp 1         allocates TMEM (4 x 128 columns); lane 0 issues the
-//                  tcgen05.mma instructions (M=128, N=128, K=16 each) and
-//                  commits each stage back to the producer;
-//   warps 2..9     epilogue: tcgen05.ld of the accumulators (each warp reads
-//                  the 32 TMEM lanes of its quadrant, half of the columns),
-//                  combination, stores.
-// Every wait is bounded by a cycle limit; on expiry the kernel records
-// LEG_ERR_TIMEOUT in the plan's status word, drains its own TMA copies and
-// MMAs (again bounded), releases TMEM and returns.
+// Kernel: persistent, CTA pairs (cluster of 2, tcgen05 cta_group::2).  A pair
+// tile is 256 operator rows (MMA M; 128 per CTA = its TMEM lanes) by tn
+// functions (MMA N, 16 <= tn <= 256; each CTA stages tn/2 of them), and
+// K advances in blocks of 32 (one 64-byte swizzle row of FP16).
+//   warp 0         TMA producer (each CTA): its operator tiles (128 rows) and
+//                  input tiles (tn/2 rows) of a K block into one of the stages,
+//                  armed on its own full barrier;
+//   warp 1         even CTA: issues the pair MMAs (M=256, N=tn, K=16) once both
+//                  CTAs' copies of a stage landed, commits each stage back to
+//                  both producers and each finished chunk to both epilogues;
+//                  odd CTA: relays its full barriers to the even CTA;
+//                  (the producer and MMA loops run on the whole warp, so that
+//                  descriptors and coordinates stay warp-uniform; one elected
+//                  lane issues the TMA, MMA and commit instructions)
+//   warps 2..17    epilogue (each CTA, own TMEM lanes): chunk promotion into
+//                  registers, then scaling and double-float stores.
+// TMEM: acc0 in columns [0, tn); acc1 in two chunk buffers [tn, 2tn) and
+// [2tn, 3tn) when tn <= 160 (the MMAs of one chunk overlap the promotion of
+// the previous one), else in one buffer [256, 256 + tn) (the MMAs pause while
+// a chunk is promoted).  Each pair MMA costs about 80 cycles to issue, so wide
+// tiles (tn up to 256, N/2 cycles of tensor work per MMA) keep the tensor
+// pipe busy.  Every wait is bounded by a cycle limit; on expiry the kernel
+// records LEG_ERR_TIMEOUT in the status word, tells the other CTA of the pair,
+// drains its own TMA copies and MMAs (again bounded), releases TMEM and returns.
 #include <stdio.h>
+#include <string.h>
+
+#include <mutex>
 
 #include "leg_fft.cuh"
 #include "leg_internal.cuh"
@@ -44,53 +65,55 @@
 
 namespace {
 
-constexpr int TILE_M = 128;   // functions per tile (TMEM lanes)
-constexpr int TILE_N = 128;   // output columns per tile
-constexpr int TILE_K = 32;    // K per stage: one 64-byte swizzle row of FP16
-constexpr int TILE_BYTES = TILE_M * TILE_K * 2;   // 8 KB (TILE_M == TILE_N)
-constexpr int EPI_WARPS = 16; // four warps per TMEM lane quadrant, 32 columns each
-constexpr int EPI_THREADS = 32 * EPI_WARPS;
-constexpr int THREADS = 64 + EPI_THREADS;
-constexpr long long DRAIN_LIMIT = 4000000000LL;   // cycles, teardown waits
+constexpr int CTA_M = 128;                          // operator rows per CTA (TMEM lanes)
+constexpr int PAIR_M = 2 * CTA_M;                   // MMA M of a CTA pair
+constexpr int TILE_K = 32;                          // K per stage: 64-byte FP16 rows
+constexpr int MAX_TN = 256;                         // functions per pair tile, at most
+constexpr int ATILE_BYTES = CTA_M * TILE_K * 2;     // 8 KB per operator plane
+constexpr int CHUNK_KB = 8;                         // K blocks per accumulation chunk of acc1
+constexpr int MAX_STAGES = 8;
+constexpr int EPI_WARPS = 16;                       // four per TMEM lane quadrant
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr size_t SMEM_LIMIT = 232448;               // opt-in shared memory per block
+constexpr size_t SMEM_STATIC_RESERVE = 1024 + 512;  // 1 KB alignment slack + static barriers
+constexpr long long DRAIN_LIMIT = 4000000000LL;     // cycles, teardown waits
 
 template <int NPROD> struct TcCfg;
-template <> struct TcCfg<8> {
-    static constexpr int NPLANES = 3;       // per operand
-    static constexpr int STAGES = 4;
-    static constexpr uint32_t TMEM_COLS = 512;
+template <> struct TcCfg<6> {
+    static constexpr int NA = LEG_SPLIT_NA, NF = LEG_SPLIT_NF, BF16 = 0;
 };
 template <> struct TcCfg<1> {
-    static constexpr int NPLANES = 1;
-    static constexpr int STAGES = 8;
-    static constexpr uint32_t TMEM_COLS = 128;
+    static constexpr int NA = 1, NF = 1, BF16 = 1;
 };
+
+// Stage layout of a launch with tiles tn functions wide: NA operator tiles
+// (128 rows x 32 K each), then NF input tiles (tn/2 rows x 32 K each), 64-byte
+// swizzled rows; a stage spans a multiple of 1 KB.
+__host__ __device__ constexpr int ftile_bytes(int tn) { return (tn / 2) * TILE_K * 2; }
 
 template <int NPROD>
-constexpr size_t tc_smem_bytes()
+__host__ __device__ constexpr int stage_bytes(int tn)
 {
-    return (size_t)TcCfg<NPROD>::STAGES * 2 * TcCfg<NPROD>::NPLANES * TILE_BYTES + 1024;
+    return (TcCfg<NPROD>::NA * ATILE_BYTES + TcCfg<NPROD>::NF * ftile_bytes(tn) + 1023) / 1024 * 1024;
 }
 
-}  // namespace
+template <int NPROD>
+constexpr int stages_for(int tn)
+{
+    const int s = (int)((SMEM_LIMIT - SMEM_STATIC_RESERVE) / (size_t)stage_bytes<NPROD>(tn));
+    return s > MAX_STAGES ? MAX_STAGES : s;
+}
 
-// One GEMM problem: out[b, j] = sum_k X[b, k] W[j, k] for b < B, j < rows,
-// with X and W given as FP16/BF16 planes through TMA maps.
-struct TcProblem {
-    CUtensorMap x[3];        // input planes   (B x Kp)
-    CUtensorMap w[3];        // operator planes (rows x Kp)
-    const int *xexp;         // per-row power-of-two scales of X (or null)
-    const int *wexp;         // per-row scales of W (or null)
-    void *out;               // float2 (double-float) or float, row stride ldo
-    int ldo, B, rows, nkb;   // nkb = Kp / TILE_K
-    int ntj;                 // tiles along j: ceil(rows / TILE_N)
-    int tile0;               // first global tile index of this problem (grouped launches)
-};
+// TMEM columns: acc0 [0, tn) for the whole tile; acc1 in one or two chunk
+// buffers: [tn (1 + b), tn (2 + b)) when three tn-wide regions fit, else [256, 256 + tn).
+__host__ __device__ constexpr int acc1_buffers(int tn) { return 3 * tn <= (int)TMEM_COLS ? 2 : 1; }
+__device__ __forceinline__ uint32_t acc1_col(int tn, int b) { return acc1_buffers(tn) == 2 ? (uint32_t)(tn * (1 + b)) : 256u; }
 
-namespace {
-
-// Tile t of a launch: its problem and its (b0, j0).
+// Pair tile t of a launch: its problem, first operator row j0, first function b0.
+// Row tiles vary fastest, so concurrent pairs share their input tiles in L2.
 __device__ __forceinline__ const TcProblem &tile_problem(const TcProblem &single, const TcProblem *multi,
-                                                         int nprob, int t, int &b0, int &j0)
+                                                         int nprob, int t, int tn, int &j0, int &b0)
 {
     const TcProblem *pr = &single;
     int lt = t;
@@ -100,232 +123,348 @@ __device__ __forceinline__ const TcProblem &tile_problem(const TcProblem &single
         pr = &multi[p];
         lt = t - pr->tile0;
     }
-    b0 = (lt / pr->ntj) * TILE_M;
-    j0 = (lt % pr->ntj) * TILE_N;
+    j0 = (lt % pr->ntm) * PAIR_M;
+    b0 = (lt / pr->ntm) * tn;
     return *pr;
 }
 
-// Persistent kernel: CTA c processes tiles c, c + gridDim.x, ...  OUT_DF: G
-// as a double-float pair (float2); else a float.  `single` describes the
-// problem of a plain launch (multi == nullptr); grouped launches pass an
-// array of problems whose tiles are numbered consecutively.
+// x 2^e: one exact multiply for normal powers of two, ldexpf beyond.
+__device__ __forceinline__ float scale2(float x, int e)
+{
+    return (e >= -126 && e <= 127) ? x * __int_as_float((e + 127) << 23) : ldexpf(x, e);
+}
+
+// Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast.
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long long limit,
+                                          const volatile int *abort_flag)
+{
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = sm100::mbar_wait_ab(bar, parity, limit, abort_flag) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// tn: functions per pair tile (multiple of 16, <= 256; every problem of the
+// launch uses it); stages: pipeline depth (<= MAX_STAGES, fits stage_bytes(tn)).
 template <int NPROD, bool OUT_DF>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcProblem single,
                                                          const TcProblem *__restrict__ multi, int nprob,
-                                                         int ntiles, int *status, long long wait_limit)
+                                                         int ntiles, int tn, int stages, int *status,
+                                                         long long wait_limit)
 {
     using Cfg = TcCfg<NPROD>;
-    constexpr int NP = Cfg::NPLANES;
-    constexpr int STAGE_BYTES = 2 * NP * TILE_BYTES;
-    constexpr uint32_t IDESC = sm100::idesc_f16(TILE_M, TILE_N, NPROD == 1 ? 1 : 0);
+    constexpr int NA = Cfg::NA, NF = Cfg::NF;
+    const int FT = ftile_bytes(tn);
+    const int SB = stage_bytes<NPROD>(tn);
+    const int nbuf = acc1_buffers(tn);
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));   // swizzle atoms need 512 B
-    __shared__ __align__(8) uint64_t full_bar[Cfg::STAGES];
-    __shared__ __align__(8) uint64_t empty_bar[Cfg::STAGES];
-    __shared__ __align__(8) uint64_t acc_full;    // MMA -> epilogue: accumulators of a tile are final
-    __shared__ __align__(8) uint64_t acc_empty;   // epilogue -> MMA: accumulators have been read
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];    // this CTA's copies of a stage landed
+    __shared__ __align__(8) uint64_t peer_bar[MAX_STAGES];    // (even CTA) the odd CTA's copies landed
+    __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];   // the pair MMAs reading a stage completed
+    __shared__ __align__(8) uint64_t chunk_full[2];           // an acc1 chunk is final
+    __shared__ __align__(8) uint64_t chunk_empty[2];          // (even CTA) both epilogues have read it
+    __shared__ __align__(8) uint64_t acc_full;                // acc0 of a tile is final
+    __shared__ __align__(8) uint64_t acc_empty;               // (even CTA) both epilogues have read it
     __shared__ __align__(8) uint64_t drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = sm100::cluster_ctarank();   // 0: MMA issuer of the pair
+    const int cid = blockIdx.x >> 1, ncl = gridDim.x >> 1;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < Cfg::STAGES; ++s) {
+        for (int s = 0; s < MAX_STAGES; ++s) {
             sm100::mbar_init(&full_bar[s], 1);
+            sm100::mbar_init(&peer_bar[s], 1);
             sm100::mbar_init(&empty_bar[s], 1);
         }
+        for (int b = 0; b < 2; ++b) {
+            sm100::mbar_init(&chunk_full[b], 1);
+            sm100::mbar_init(&chunk_empty[b], 2 * EPI_WARPS);
+        }
         sm100::mbar_init(&acc_full, 1);
-        sm100::mbar_init(&acc_empty, EPI_THREADS);
+        sm100::mbar_init(&acc_empty, 2 * EPI_WARPS);
         sm100::mbar_init(&drain_bar, 1);
         s_abort = 0;
         sm100::fence_mbar_init();
         if (!multi) {
-            for (int p = 0; p < NP; ++p) {
-                sm100::prefetch_tmap(&single.x[p]);
-                sm100::prefetch_tmap(&single.w[p]);
-            }
+            sm100::prefetch_tmap(&single.a);
+            sm100::prefetch_tmap(&single.f);
         }
     }
     if (warp == 1) {
-        sm100::tmem_alloc(&tmem_slot, Cfg::TMEM_COLS);
+        sm100::tmem_alloc_pair(&tmem_slot, TMEM_COLS);
         sm100::tc_fence_before();
     }
-    __syncthreads();
+    sm100::cluster_sync();
     sm100::tc_fence_after();
     const uint32_t tmem = tmem_slot;
 
-    if (warp == 0 && lane == 0) {
-        // ------------------------------------------------ TMA producer
-        uint32_t it = 0;   // stage-ring position, continues across tiles
-        for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x) {
-            int b0, j0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, t, b0, j0);
-            const int nkb = pr.nkb;
-            bool ok = true;
-            for (int kb = 0; kb < nkb; ++kb, ++it) {
-                const int s = it % Cfg::STAGES;
-                const uint32_t ph = (it / Cfg::STAGES) & 1;
-                if (!sm100::mbar_wait(&empty_bar[s], ph ^ 1, wait_limit)) {
+    const uint32_t peer_abort = sm100::mapa_shared(sm100::smem_u32(const_cast<int *>(&s_abort)), rank ^ 1u);
+    auto fail = [&]() {
+        atomicOr(status, 1);
+        s_abort = 1;
+        sm100::st_cluster_u32(peer_abort, 1u);
+    };
+
+    if (warp == 0) {
+        // ------------------------------------------------ TMA producer warp (both CTAs)
+        const bool leader = sm100::elect_one();
+        uint32_t s = 0, ph = 0, issued = 0;   // stage ring position, continues across tiles
+        bool ok = true;
+        const int half = tn >> 1;
+        const uint32_t bytes = NA * ATILE_BYTES + NF * FT;
+        for (int t = cid; ok && t < ntiles; t += ncl) {
+            int j0, b0;
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
+            const int arow = j0 + (int)rank * CTA_M, frow = b0 + (int)rank * half;
+            for (int kb = 0; kb < pr.nkb; ++kb) {
+                if (!warp_wait(&empty_bar[s], ph ^ 1, wait_limit, &s_abort)) {
                     ok = false;
                     break;
                 }
-                unsigned char *st = smem + s * STAGE_BYTES;
-                sm100::mbar_arrive_expect_tx(&full_bar[s], STAGE_BYTES);
-                for (int p = 0; p < NP; ++p)
-                    sm100::tma_load_2d(st + p * TILE_BYTES, &pr.x[p], &full_bar[s], kb * TILE_K, b0);
-                for (int p = 0; p < NP; ++p)
-                    sm100::tma_load_2d(st + (NP + p) * TILE_BYTES, &pr.w[p], &full_bar[s], kb * TILE_K, j0);
-            }
-            if (!ok) {
-                atomicOr(status, 1);
-                s_abort = 1;
-                break;
+                if (leader) {
+                    // one box per plane (third coordinate) of each operand
+                    unsigned char *st = smem + s * SB;
+                    sm100::mbar_arrive_expect_tx(&full_bar[s], bytes);
+#pragma unroll
+                    for (int p = 0; p < NA; ++p)
+                        sm100::tma_load_3d(st + p * ATILE_BYTES, &pr.a, &full_bar[s], kb * TILE_K, arow, p);
+#pragma unroll
+                    for (int p = 0; p < NF; ++p)
+                        sm100::tma_load_3d(st + NA * ATILE_BYTES + p * FT, &pr.f, &full_bar[s], kb * TILE_K, frow, p);
+                }
+                __syncwarp();
+                ++issued;
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1;
+                }
             }
         }
-        // drain: the last copy issued into every stage has landed before exit
-        const uint32_t first = it > (uint32_t)Cfg::STAGES ? it - Cfg::STAGES : 0;
-        for (uint32_t i = first; i < it; ++i)
-            sm100::mbar_wait(&full_bar[i % Cfg::STAGES], (i / Cfg::STAGES) & 1, DRAIN_LIMIT);
-    } else if (warp == 1 && lane == 0) {
-        // ------------------------------------------------ MMA issuer
-        uint32_t it = 0;
+        if (lane == 0) {
+            if (!ok) fail();
+            // drain: the last copy issued into every stage has landed before exit
+            const uint32_t first = issued > (uint32_t)stages ? issued - stages : 0;
+            for (uint32_t i = first; i < issued; ++i)
+                sm100::mbar_wait(&full_bar[i % stages], (i / stages) & 1, DRAIN_LIMIT);
+        }
+    } else if (warp == 1 && rank == 0) {
+        // ------------------------------------------------ MMA warp (even CTA)
+        const bool leader = sm100::elect_one();
+        uint32_t s = 0, ph = 0, cc = 0;   // stage ring position, acc1 chunk counter
+        bool ok = true;
+        const uint32_t idesc = sm100::idesc_f16(PAIR_M, tn, Cfg::BF16);
         int ti = 0;
-        for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++ti) {
-            int b0, j0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, t, b0, j0);
-            const int nkb = pr.nkb;
-            bool ok = sm100::mbar_wait(&acc_empty, (ti & 1) ^ 1, wait_limit);   // previous tile drained
+        for (int t = cid; ok && t < ntiles; t += ncl, ++ti) {
+            int j0, b0;
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
+            // acc0 of the previous tile has been read by both epilogues
+            if (!warp_wait(&acc_empty, (ti & 1) ^ 1, wait_limit, &s_abort)) {
+                ok = false;
+                break;
+            }
             sm100::tc_fence_after();
-            for (int kb = 0; ok && kb < nkb; ++kb, ++it) {
-                const int s = it % Cfg::STAGES;
-                const uint32_t ph = (it / Cfg::STAGES) & 1;
-                if (!sm100::mbar_wait(&full_bar[s], ph, wait_limit)) {
+            uint32_t acc1 = tmem + 256;
+            for (int kb = 0; kb < pr.nkb; ++kb) {
+                if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort) ||
+                    !warp_wait(&peer_bar[s], ph, wait_limit, &s_abort)) {
                     ok = false;
                     break;
                 }
                 sm100::tc_fence_after();
-                const uint32_t st = sm100::smem_u32(smem + s * STAGE_BYTES);
+                // descriptors: the stage base once, planes and K-steps as offsets
+                // of the 16-byte address field (addresses stay below 2^18)
+                const uint64_t d0 = sm100::desc_k_sw64(sm100::smem_u32(smem + s * SB));
+                auto A = [&](int p, int kk) { return d0 + (uint64_t)((p * ATILE_BYTES + kk * 32) >> 4); };
+                auto F = [&](int p, int kk) { return d0 + (uint64_t)((NA * ATILE_BYTES + p * FT + kk * 32) >> 4); };
+                // acc0 (weight 1): A0 F0, accumulated over the whole tile
+                if (leader) {
 #pragma unroll
-                for (int kk = 0; kk < TILE_K / 16; ++kk) {
-                    const uint32_t koff = kk * 32;   // 16 FP16 = 32 bytes along K
-                    const uint32_t acc = (kb == 0 && kk == 0) ? 0u : 1u;
-                    auto X = [&](int p) { return sm100::desc_k_sw64(st + p * TILE_BYTES + koff); };
-                    auto W = [&](int p) { return sm100::desc_k_sw64(st + (NP + p) * TILE_BYTES + koff); };
-                    if constexpr (NPROD == 1) {
-                        sm100::mma_f16(tmem, X(0), W(0), IDESC, acc);
-                    } else {
-                        const uint32_t a1 = tmem + TILE_N, a2 = tmem + 2 * TILE_N, a3 = tmem + 3 * TILE_N;
-                        sm100::mma_f16(tmem, X(0), W(0), IDESC, acc);   // F0 A0   (weight 1)
-                        sm100::mma_f16(a1, X(0), W(1), IDESC, acc);     // F0 A1   (2^-s)
-                        sm100::mma_f16(a1, X(1), W(0), IDESC, 1u);      // F1 A0
-                        sm100::mma_f16(a2, X(1), W(1), IDESC, acc);     // F1 A1   (2^-2s)
-                        sm100::mma_f16(a2, X(0), W(2), IDESC, 1u);      // F0 A2s
-                        sm100::mma_f16(a2, X(2), W(0), IDESC, 1u);      // F2s A0
-                        sm100::mma_f16(a3, X(1), W(2), IDESC, acc);     // F1 A2s  (2^-3s)
-                        sm100::mma_f16(a3, X(2), W(1), IDESC, 1u);      // F2s A1
-                    }
+                    for (int kk = 0; kk < TILE_K / 16; ++kk)
+                        sm100::mma_f16_pair(tmem, A(0, kk), F(0, kk), idesc, (kb == 0 && kk == 0) ? 0u : 1u);
                 }
-                sm100::mma_commit(&empty_bar[s]);
+                if constexpr (NPROD > 1) {
+                    const int kc = kb % CHUNK_KB;
+                    if (kc == 0) {   // a new acc1 chunk: its buffer must have been read
+                        const uint32_t b = cc % nbuf, u = cc / nbuf;
+                        if (!warp_wait(&chunk_empty[b], (u & 1) ^ 1, wait_limit, &s_abort)) {
+                            ok = false;
+                            break;
+                        }
+                        sm100::tc_fence_after();
+                        acc1 = tmem + acc1_col(tn, (int)b);
+                    }
+                    if (leader) {
+#pragma unroll
+                        for (int kk = 0; kk < TILE_K / 16; ++kk) {
+                            // acc1 (weight 2^-s): five products, the 2^-2s terms via pre-scaled inputs
+                            sm100::mma_f16_pair(acc1, A(1, kk), F(0, kk), idesc, (kc == 0 && kk == 0) ? 0u : 1u);
+                            sm100::mma_f16_pair(acc1, A(0, kk), F(1, kk), idesc, 1u);   // A0 F1
+                            sm100::mma_f16_pair(acc1, A(0, kk), F(2, kk), idesc, 1u);   // A0 (r - F1)
+                            sm100::mma_f16_pair(acc1, A(1, kk), F(3, kk), idesc, 1u);   // A1 2^-s F1
+                            sm100::mma_f16_pair(acc1, A(2, kk), F(4, kk), idesc, 1u);   // A2s 2^-s F0
+                        }
+                        sm100::mma_commit_pair_mc(&empty_bar[s], 0x3);
+                        if (kc == CHUNK_KB - 1 || kb == pr.nkb - 1) sm100::mma_commit_pair_mc(&chunk_full[cc % nbuf], 0x3);
+                    }
+                    if (kc == CHUNK_KB - 1 || kb == pr.nkb - 1) ++cc;
+                } else {
+                    if (leader) sm100::mma_commit_pair_mc(&empty_bar[s], 0x3);
+                }
+                __syncwarp();
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1;
+                }
             }
-            if (!ok) {
-                atomicOr(status, 1);
-                s_abort = 1;
-                break;
-            }
-            sm100::mma_commit(&acc_full);
+            if (!ok) break;
+            if (leader) sm100::mma_commit_pair_mc(&acc_full, 0x3);
+            __syncwarp();
         }
-        // every MMA issued by this thread has completed before TMEM is released
-        sm100::mma_commit(&drain_bar);
-        sm100::mbar_wait(&drain_bar, 0, DRAIN_LIMIT);
-    } else if (warp >= 2) {
-        // ------------------------------------------------ epilogue
-        const int q = warp & 3;                        // TMEM lane quadrant of this warp
-        const int c0 = ((warp - 2) >> 2) * 32;         // this warp's 32 columns
-        const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16) + c0;
+        if (leader) {
+            if (!ok) fail();
+            // every MMA issued by this lane has completed before TMEM is released
+            sm100::mma_commit_pair_mc(&drain_bar, 0x1);
+            sm100::mbar_wait(&drain_bar, 0, DRAIN_LIMIT);
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ relay warp (odd CTA)
+        const uint32_t peer0 = sm100::mapa_shared(sm100::smem_u32(&peer_bar[0]), 0u);
+        uint32_t s = 0, ph = 0;
+        bool ok = true;
+        for (int t = cid; ok && t < ntiles; t += ncl) {
+            int j0, b0;
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
+            for (int kb = 0; kb < pr.nkb; ++kb) {
+                if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) sm100::mbar_arrive_cluster(peer0 + 8u * s);
+                __syncwarp();
+                if (++s == (uint32_t)stages) {
+                    s = 0;
+                    ph ^= 1;
+                }
+            }
+        }
+        if (!ok && lane == 0) fail();
+    } else {
+        // ------------------------------------------------ epilogue (both CTAs)
+        // Warp (quadrant q, group cg) owns TMEM lanes 32q.. (operator rows) and the
+        // 16-column units cg, cg + 4, cg + 8, cg + 12 below tn (functions).
+        const int q = warp & 3;
+        const int cg = (warp - 2) >> 2;
+        const uint32_t lane_base = tmem + ((uint32_t)(q * 32) << 16);
+        const uint32_t chunk_empty0 = sm100::mapa_shared(sm100::smem_u32(&chunk_empty[0]), 0u);
+        const uint32_t acc_empty0 = sm100::mapa_shared(sm100::smem_u32(&acc_empty), 0u);
+        const int nunits = tn >> 4;
+        constexpr float W1 = 1.0f / (float)(1 << LEG_SPLIT_FBITS);
+        uint32_t cc = 0;
         int ti = 0;
-        for (int t = blockIdx.x; t < ntiles && !s_abort; t += gridDim.x, ++ti) {
-            int b0, j0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, t, b0, j0);
-            if (!sm100::mbar_wait(&acc_full, ti & 1, wait_limit)) {
-                atomicOr(status, 1);
-                s_abort = 1;
+        bool ok = true;
+        for (int t = cid; ok && t < ntiles; t += ncl, ++ti) {
+            int j0, b0;
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
+            // per-function scales of this warp's columns: lane l holds unit m's
+            // column (l & 15); fetched before the accumulators are ready
+            int fe[4] = {0, 0, 0, 0};
+            if (NPROD > 1 && pr.fexp) {
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const int bi = b0 + (cg + 4 * m) * 16 + (lane & 15);
+                    if (cg + 4 * m < nunits && bi < pr.B) fe[m] = pr.fexp[bi];
+                }
+            }
+            float r1[64];
+#pragma unroll
+            for (int i = 0; i < 64; ++i) r1[i] = 0.0f;
+            if constexpr (NPROD > 1) {
+                const int nch = (pr.nkb + CHUNK_KB - 1) / CHUNK_KB;
+                for (int ch = 0; ch < nch; ++ch, ++cc) {
+                    const uint32_t b = cc % nbuf, u = cc / nbuf;
+                    if (!warp_wait(&chunk_full[b], u & 1, wait_limit, &s_abort)) {
+                        ok = false;
+                        break;
+                    }
+                    __syncwarp();
+                    sm100::tc_fence_after();
+                    const uint32_t base = lane_base + acc1_col(tn, (int)b);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (cg + 4 * m < nunits) {
+                            float tv[16];
+                            sm100::tmem_ld_32x32b_x16(base + (uint32_t)((cg + 4 * m) * 16), tv);
+                            sm100::tmem_ld_wait();
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) r1[16 * m + i] += tv[i];
+                        }
+                    }
+                    sm100::tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) sm100::mbar_arrive_cluster(chunk_empty0 + 8u * b);
+                }
+                if (!ok) break;
+            }
+            if (!warp_wait(&acc_full, ti & 1, wait_limit, &s_abort)) {
+                ok = false;
                 break;
             }
+            __syncwarp();
             sm100::tc_fence_after();
-            float a0[32], a1[32];
-            sm100::tmem_ld_32x32b_x32(lane_addr, a0);
-            if constexpr (NPROD == 8) {
-                // fold the small accumulators: a1 <- 2^-s acc1 + 2^-2s acc2 + 2^-3s acc3
-                constexpr float W1 = 1.0f / (float)(1 << LEG_SPLIT_FBITS);
-                sm100::tmem_ld_32x32b_x32(lane_addr + TILE_N, a1);
+            const int j = j0 + (int)rank * CTA_M + q * 32 + lane;
+            const bool row_ok = j < pr.rows;
+            const int ej = (row_ok && pr.aexp) ? pr.aexp[j] : 0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                if (cg + 4 * m >= nunits) continue;
+                float tv[16];
+                sm100::tmem_ld_32x32b_x16(lane_base + (uint32_t)((cg + 4 * m) * 16), tv);
                 sm100::tmem_ld_wait();
+                const int bb = b0 + (cg + 4 * m) * 16;
 #pragma unroll
-                for (int h = 0; h < 32; h += 16) {
-                    float tq[16];
-                    sm100::tmem_ld_32x32b_x16(lane_addr + 2 * TILE_N + h, tq);
-                    sm100::tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) a1[h + i] = fmaf(tq[i], W1 * W1, a1[h + i] * W1);
-                    sm100::tmem_ld_32x32b_x16(lane_addr + 3 * TILE_N + h, tq);
-                    sm100::tmem_ld_wait();
-#pragma unroll
-                    for (int i = 0; i < 16; ++i) a1[h + i] = fmaf(tq[i], W1 * W1 * W1, a1[h + i]);
+                for (int i = 0; i < 16; ++i) {
+                    const int e = ej + __shfl_sync(0xffffffffu, fe[m], i);
+                    const int bi = bb + i;
+                    if (!row_ok || bi >= pr.B) continue;
+                    const size_t o = (size_t)bi * pr.ldo + j;
+                    if constexpr (NPROD == 1) {
+                        static_cast<float *>(pr.out)[o] = tv[i];
+                    } else if constexpr (OUT_DF) {
+                        const dfl sm = df_two_sum(tv[i], r1[16 * m + i] * W1);
+                        static_cast<float2 *>(pr.out)[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
+                    } else {
+                        static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], W1, tv[i]), e);
+                    }
                 }
-            } else {
-                sm100::tmem_ld_wait();
             }
-            // accumulators read: the MMA warp may start the next tile
+            // acc0 read: the MMA warp may start the next tile
             sm100::tc_fence_before();
-            sm100::mbar_arrive(&acc_empty);
-
-            const int b = b0 + q * 32 + lane;
-            if (b >= pr.B) continue;
-            const int jb = j0 + c0;
-            const int rows = pr.rows;
-            const int eb = (pr.xexp != nullptr) ? pr.xexp[b] : 0;
-            if constexpr (OUT_DF) {
-                float2 *o = static_cast<float2 *>(pr.out) + (size_t)b * pr.ldo + jb;
-#pragma unroll
-                for (int i = 0; i < 32; i += 2) {
-                    float2 r[2];
-#pragma unroll
-                    for (int u = 0; u < 2; ++u) {
-                        const int j = jb + i + u;
-                        const int e = eb + ((j < rows) ? pr.wexp[j] : 0);
-                        dfl sum = df_two_sum(a0[i + u], a1[i + u]);
-                        r[u] = make_float2(ldexpf(sum.hi, e), ldexpf(sum.lo, e));
-                    }
-                    if (jb + i + 1 < rows) {
-                        *reinterpret_cast<float4 *>(o + i) = make_float4(r[0].x, r[0].y, r[1].x, r[1].y);
-                    } else if (jb + i < rows) {
-                        o[i] = r[0];
-                    }
-                }
-            } else {
-                float *o = static_cast<float *>(pr.out) + (size_t)b * pr.ldo + jb;
-#pragma unroll
-                for (int i = 0; i < 32; ++i) {
-                    const int j = jb + i;
-                    if (j >= rows) break;
-                    if constexpr (NPROD == 8) o[i] = ldexpf(a0[i] + a1[i], eb + pr.wexp[j]);
-                    else o[i] = a0[i];
-                }
-            }
+            __syncwarp();
+            if (lane == 0) sm100::mbar_arrive_cluster(acc_empty0);
         }
+        if (!ok && lane == 0) fail();
     }
+    __syncwarp();
     sm100::tc_fence_before();
-    __syncthreads();
-    if (warp == 1) sm100::tmem_dealloc(tmem, Cfg::TMEM_COLS);
+    sm100::cluster_sync();
+    if (warp == 1) {
+        sm100::tc_fence_after();
+        sm100::tmem_dealloc_pair(tmem, TMEM_COLS);
+    }
 }
 
 // ---------------------------------------------------------------- input split
 // One CTA per row: power-of-two scale 2^e >= max|x|, then with s = LEG_SPLIT_FBITS
-//   xs = x 2^-e,  X0 = round(xs 2^s) 2^-s,  r1 = (xs - X0) 2^s,  X1 = fp16(r1),
-//   X2s = fp16((r1 - X1) 2^s),   so xs = X0 + 2^-s X1 + 2^-2s X2s.
-// Input either FP32 (forward) or a double-float pair (adjoint).
+//   xs = x 2^-e,  F0 = round(xs 2^s) 2^-s,  r = (xs - F0) 2^s,  F1 = fp16(r),
+// and the five planes  F0, F1, fp16(r - F1), fp16(2^-s F1), 2^-s F0  (plane p
+// at P + p * pstride), so that xs = F0 + 2^-s (F1 + (r - F1)).  Input FP32
+// (forward) or a double-float pair (adjoint).  g0 (forward only): row 0 of G,
+// a00 * x[0] as a double-float pair (the operator's row 0 is a00 e_0).
 template <class T> __device__ __forceinline__ float hi_of(T v);
 template <> __device__ __forceinline__ float hi_of<float>(float v) { return v; }
 template <> __device__ __forceinline__ float hi_of<float2>(float2 v) { return v.x; }
@@ -333,48 +472,89 @@ template <class T> __device__ __forceinline__ float lo_of(T v);
 template <> __device__ __forceinline__ float lo_of<float>(float) { return 0.0f; }
 template <> __device__ __forceinline__ float lo_of<float2>(float2 v) { return v.y; }
 
+constexpr int SPLIT_THREADS = 128;
+
+// The CTA splits one row: n values, zero-padded to np (a multiple of 8).
+// Pass 1 reduces max |x|; pass 2 handles 8 consecutive elements per thread and
+// writes each plane's 8 FP16 values as one 16-byte store.
 template <class T>
-__global__ void __launch_bounds__(256) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
-                                                         __half *__restrict__ X0, __half *__restrict__ X1,
-                                                         __half *__restrict__ X2, int *__restrict__ xexp)
+__device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
+                                          size_t pstride, int *__restrict__ xexp, float2 *g0, double a00)
 {
-    const int b = blockIdx.x;
-    const T *row = x + (size_t)b * ldx;
-    __shared__ float red[8];
+    __shared__ float red[SPLIT_THREADS / 32];
     __shared__ int s_e;
     float m = 0.0f;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) m = fmaxf(m, fabsf(hi_of(row[k])));
+    for (int k = threadIdx.x; k < n; k += SPLIT_THREADS) m = fmaxf(m, fabsf(hi_of(row[k])));
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
     if (threadIdx.x == 0) {
         float mm = 0.0f;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mm = fmaxf(mm, red[w]);
+        for (int w = 0; w < SPLIT_THREADS / 32; ++w) mm = fmaxf(mm, red[w]);
         int e = 0;
         if (mm > 0.0f) {
             float fr = frexpf(mm, &e);       // mm = fr 2^e, fr in [0.5, 1)
-            if (fr == 0.5f) e -= 1;         // scaled |hi| <= 1, hence |X0| <= 1
+            if (fr == 0.5f) e -= 1;          // scaled |hi| <= 1, hence |F0| <= 1
         }
         s_e = e;
-        xexp[b] = e;
+        *xexp = e;
+        if (g0) {
+            const double v = (double)hi_of(row[0]) * a00;
+            const float h = __double2float_rn(v);
+            *g0 = make_float2(h, __double2float_rn(v - (double)h));
+        }
     }
     __syncthreads();
     const int e = s_e;
-    const size_t o = (size_t)b * np;
-    for (int k = threadIdx.x; k < np; k += blockDim.x) {
-        float h = 0.0f, l = 0.0f;
-        if (k < n) {
-            h = ldexpf(hi_of(row[k]), -e);
-            l = ldexpf(lo_of(row[k]), -e);
+    constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
+    for (int c = threadIdx.x; c < np / 8; c += SPLIT_THREADS) {
+        __align__(16) __half o[LEG_SPLIT_NF][8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * c + i;
+            float h = 0.0f, l = 0.0f;
+            if (k < n) {
+                const T v = row[k];
+                h = ldexpf(hi_of(v), -e);
+                l = ldexpf(lo_of(v), -e);
+            }
+            const float x0 = rintf(h * SC) * ISC;
+            const float r = (h - x0) * SC + l * SC;
+            const __half f1 = __float2half_rn(r);
+            const float f1f = __half2float(f1);
+            o[0][i] = __float2half_rn(x0);
+            o[1][i] = f1;
+            o[2][i] = __float2half_rn(r - f1f);
+            o[3][i] = __float2half_rn(f1f * ISC);
+            o[4][i] = __float2half_rn(x0 * ISC);
         }
-        constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
-        float x0 = rintf(h * SC) * ISC;
-        float r1 = (h - x0) * SC + l * SC;
-        __half h1 = __float2half_rn(r1);
-        X0[o + k] = __float2half_rn(x0);
-        X1[o + k] = h1;
-        X2[o + k] = __float2half_rn((r1 - __half2float(h1)) * SC);
+#pragma unroll
+        for (int p = 0; p < LEG_SPLIT_NF; ++p)
+            *reinterpret_cast<uint4 *>(P + p * pstride + 8 * c) = *reinterpret_cast<const uint4 *>(o[p]);
     }
+}
+
+template <class T>
+__global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
+                                                                   LegSplitIn in, float2 *G, int ldg, double a00)
+{
+    const int b = blockIdx.x;
+    split_row<T>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
+                 G ? G + (size_t)b * ldg : nullptr, a00);
+}
+
+// Ragged batch: function i (one CTA) goes to row row[i] of bucket bucket[i].
+__global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float *__restrict__ f_packed,
+                                                                     const long long *__restrict__ in_off,
+                                                                     const int *__restrict__ bucket,
+                                                                     const int *__restrict__ row,
+                                                                     const LegRaggedBucket *__restrict__ bk)
+{
+    const int i = blockIdx.x;
+    const LegRaggedBucket &b = bk[bucket[i]];
+    const int r = row[i];
+    split_row<float>(f_packed + in_off[i], b.K, b.Kp, b.in.base + (size_t)r * b.in.ld, b.in.pstride,
+                     b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00);
 }
 
 __global__ void __launch_bounds__(256) bf16_rows_kernel(const float *__restrict__ x, int n, int np,
@@ -387,7 +567,7 @@ __global__ void __launch_bounds__(256) bf16_rows_kernel(const float *__restrict_
 
 // Transposed split planes of the operator for the adjoint GEMM: row k of the
 // result is column k of A (j = 0..rows-1, zero-padded to npr), scaled by
-// 2^e_k >= sum_j |A[j,k]|, split as in plane_split_kernel.
+// 2^e_k >= sum_j |A[j,k]|, split as the operator's own planes.
 __global__ void __launch_bounds__(256) split_cols_kernel(const double *__restrict__ A, int rows, int K, int npr,
                                                          __half *__restrict__ T0, __half *__restrict__ T1,
                                                          __half *__restrict__ T2, int *__restrict__ colexp)
@@ -448,18 +628,21 @@ int get_encoder(EncodeTiledFn *fn)
     return LEG_OK;
 }
 
-// 2-D map over a [outer x inner] 16-bit array with row stride ld (elements);
-// box = 32 (inner) x 128 (outer), 64-byte swizzle, zero fill out of bounds.
-int make_map(CUtensorMap *m, const void *base, int inner, int outer, int ld, bool bf16)
+// 3-D map over `planes` [outer x inner] 16-bit arrays with row stride ld and
+// plane stride pstride (elements); box = 32 (inner) x box_outer x 1 plane,
+// 64-byte swizzle, zero fill out of bounds: one copy per plane and K block
+// (several smaller copies in flight load a stage faster than one large box).
+int make_map(CUtensorMap *m, const void *base, int inner, int outer, int ld, int planes, size_t pstride, bool bf16,
+             int box_outer)
 {
     EncodeTiledFn enc;
     int rc = get_encoder(&enc);
     if (rc) return rc;
-    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {TILE_K, TILE_M};   // 32 x 16 bit = 64 B rows
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+    cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)planes};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 2, (cuuint64_t)pstride * 2};
+    cuuint32_t box[3] = {TILE_K, (cuuint32_t)box_outer, 1};   // 32 x 16 bit = 64 B rows
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3,
                      const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -467,87 +650,231 @@ int make_map(CUtensorMap *m, const void *base, int inner, int outer, int ld, boo
     return LEG_OK;
 }
 
+// Number of CTA pairs of the split kernel that can be resident at once on
+// the current device (queried once per device, at the largest shared-memory
+// footprint, which allows one CTA per SM).
+int max_pairs(int *out)
+{
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    LEG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return leg_set_error(LEG_ERR_INVALID_ARG, "device index out of range");
+    std::lock_guard<std::mutex> lock(mu);
+    if (!cache[dev]) {
+        auto kern = tc_gemm_kernel<6, true>;
+        const size_t smem = SMEM_LIMIT - SMEM_STATIC_RESERVE + 1024;
+        LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(THREADS, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int n = 0;
+        LEG_CUDA_TRY(cudaOccupancyMaxActiveClusters(&n, (const void *)kern, &cfg));
+        if (n < 1) return leg_set_error(LEG_ERR_CUDA, "no CTA pair of the tensor-core GEMM fits on this device");
+        cache[dev] = n;
+    }
+    *out = cache[dev];
+    return LEG_OK;
+}
+
 template <int NPROD, bool OUT_DF>
-int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int ntiles, int *status, long long limit,
-              cudaStream_t st)
+int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int ntiles, int tn, int *status,
+              long long limit, cudaStream_t st)
 {
     if (ntiles <= 0) return LEG_OK;
+    if (tn < 16 || tn > MAX_TN || tn % 16) return leg_set_error(LEG_ERR_INVALID_ARG, "tile width out of range");
     auto kern = tc_gemm_kernel<NPROD, OUT_DF>;
-    const size_t smem = tc_smem_bytes<NPROD>();
+    const int stages = stages_for<NPROD>(tn);
+    const size_t smem = (size_t)stages * stage_bytes<NPROD>(tn) + 1024;
     LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    static int num_sms = 0;
-    if (!num_sms) {
-        int dev = 0;
-        LEG_CUDA_TRY(cudaGetDevice(&dev));
-        LEG_CUDA_TRY(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    }
-    const int grid = ntiles < num_sms ? ntiles : num_sms;
-    kern<<<grid, THREADS, smem, st>>>(single, multi, nprob, ntiles, status, limit);
-    LEG_LAUNCH_CHECK("tc_gemm_kernel");
+    int pairs = 0;
+    int rc = max_pairs(&pairs);
+    if (rc) return rc;
+    const int npairs = ntiles < pairs ? ntiles : pairs;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * npairs, 1, 1);
+    cfg.blockDim = dim3(THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, single, multi, nprob, ntiles, tn, stages, status, limit));
     return LEG_OK;
 }
 
-// A single-problem descriptor; maps over planes with row stride ld.
-int make_problem(TcProblem *pr, __half *const xs[3], int xrows, const __half *const ws[3], int wrows, int Kp,
-                 const int *xexp, const int *wexp, void *out, int ldo, int B, int rows)
+// Cycles of one pair MMA (M = 256, N = tn, K = 16) on each SM of the pair:
+// the slowest of the tensor rate (128 x tn x 16 MACs at 4096 per cycle), the
+// operand reads from shared memory (4 KB of A plus tn/2 rows of B at 128
+// bytes per cycle) and the issue cost of one pair instruction (about 80
+// cycles, measured on GB300 for tn = 32..128 with CUDA-event and clock64
+// timings of this kernel).
+int mma_cycles(int tn)
 {
-    int rc;
-    for (int s = 0; s < 3; ++s) {
-        if ((rc = make_map(&pr->x[s], xs[s], Kp, xrows, Kp, false))) return rc;
-        if ((rc = make_map(&pr->w[s], ws[s], Kp, wrows, Kp, false))) return rc;
+    int c = tn / 2;
+    if (32 + tn / 8 > c) c = 32 + tn / 8;
+    if (80 > c) c = 80;
+    return c;
+}
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+// Estimated cycles of the busiest pair for ntm row tiles x B functions with
+// K-depth nkb: waves x (per-tile fixed cost + nkb x (12 MMAs + the acc1
+// promotion stall when acc1 has a single TMEM buffer)).
+long long tile_cost(int tn, int ntm, int B, int nkb, int pairs)
+{
+    const long long tiles = (long long)ntm * ceil_div(B, tn);
+    const long long waves = (tiles + pairs - 1) / pairs;
+    const long long promo = acc1_buffers(tn) == 1 ? (400 + 3 * tn) / CHUNK_KB : 0;
+    return waves * (2000 + (long long)nkb * (12 * mma_cycles(tn) + promo));
+}
+
+// Functions per pair tile: the lowest tile_cost, ties to the wider tile.
+int choose_tn(int ntm, int B, int nkb, int pairs)
+{
+    int best = MAX_TN;
+    long long best_cost = -1;
+    for (int tn = MAX_TN; tn >= 16; tn -= 16) {
+        const long long cost = tile_cost(tn, ntm, B, nkb, pairs);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best = tn;
+        }
     }
-    pr->xexp = xexp;
-    pr->wexp = wexp;
+    return best;
+}
+
+void finish_problem(TcProblem *pr, const int *aexp, const int *fexp, void *out, int ldo, int rows, int B, int Kc,
+                    int tn)
+{
+    pr->aexp = aexp;
+    pr->fexp = fexp;
     pr->out = out;
     pr->ldo = ldo;
-    pr->B = B;
     pr->rows = rows;
-    pr->nkb = Kp / TILE_K;
-    pr->ntj = (rows + TILE_N - 1) / TILE_N;
+    pr->B = B;
+    pr->nkb = Kc / TILE_K;
+    pr->tn = tn;
+    pr->ntm = ceil_div(rows, PAIR_M);
+    pr->ntn = ceil_div(B, tn);
     pr->tile0 = 0;
+}
+
+// Split problem: operator planes a0 + s apstride (rows x Kc, row stride lda),
+// input planes of `in`.
+int make_split(TcProblem *pr, const __half *a0, size_t apstride, int rows, int lda, const int *aexp,
+               const LegSplitIn &in, int B, int Kc, void *out, int ldo, int tn)
+{
+    int rc;
+    if ((rc = make_map(&pr->a, a0, Kc, rows, lda, LEG_SPLIT_NA, apstride, false, CTA_M))) return rc;
+    if ((rc = make_map(&pr->f, in.base, Kc, B, in.ld, LEG_SPLIT_NF, in.pstride, false, tn / 2))) return rc;
+    finish_problem(pr, aexp, in.fexp, out, ldo, rows, B, Kc, tn);
     return LEG_OK;
 }
 
-int tiles_of(const TcProblem &pr) { return ((pr.B + TILE_M - 1) / TILE_M) * pr.ntj; }
+int tiles_of(const TcProblem &pr) { return pr.ntm * pr.ntn; }
 
 }  // namespace
+
+LegSplitIn leg_split_workspace(const leg_plan *p)
+{
+    LegSplitIn in;
+    in.base = p->Fh;
+    in.pstride = (size_t)p->ws_B * p->ldf;
+    in.ld = p->ldf;
+    in.fexp = p->fexp;
+    return in;
+}
+
+int leg_split_max_pairs(int *pairs) { return max_pairs(pairs); }
+
+long long leg_split_tile_cost(int tn, int ntm, int B, int nkb, int pairs) { return tile_cost(tn, ntm, B, nkb, pairs); }
+
+int leg_split_choose_tn(const leg_plan *p, int B)
+{
+    if (p->tn) return p->tn;
+    int pairs = 0;
+    if (max_pairs(&pairs)) return MAX_TN;
+    return choose_tn(ceil_div(p->rows - 1, PAIR_M), B, p->Kp / TILE_K, pairs);
+}
 
 int leg_build_split_transposed(leg_plan *p)
 {
     const int npr = leg_round_up(leg_round_up(p->rows, 8), LEG_KPAD);
-    for (int s = 0; s < 3; ++s) LEG_CUDA_TRY(cudaMalloc(&p->AhT[s], sizeof(__half) * (size_t)p->K * npr));
+    const size_t plane = (size_t)p->K * npr;
+    LEG_CUDA_TRY(cudaMalloc(&p->AhT[0], sizeof(__half) * 3 * plane));
+    p->AhT[1] = p->AhT[0] + plane;
+    p->AhT[2] = p->AhT[0] + 2 * plane;
     LEG_CUDA_TRY(cudaMalloc(&p->colexp, sizeof(int) * p->K));
     split_cols_kernel<<<p->K, 256>>>(p->A64, p->rows, p->K, npr, p->AhT[0], p->AhT[1], p->AhT[2], p->colexp);
     LEG_LAUNCH_CHECK("split_cols_kernel");
     return LEG_OK;
 }
 
-int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
+int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const LegSplitIn &in, float2 *G,
+                                 int ldg, cudaStream_t st)
 {
-    split_rows_kernel<float><<<B, 256, 0, st>>>(f, p->K, p->K, p->Kp, p->Fh[0], p->Fh[1], p->Fh[2], p->fexp);
+    split_rows_kernel<float><<<B, SPLIT_THREADS, 0, st>>>(f, p->K, p->K, p->Kp, in, G, ldg, p->a00);
     LEG_LAUNCH_CHECK("split_rows_kernel");
     return LEG_OK;
 }
 
-int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st)
+int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
+{
+    return leg_split_prepare_input_into(p, f, B, leg_split_workspace(p), static_cast<float2 *>(p->G), p->ldg, st);
+}
+
+// Forward split problem: operator rows 1..rows-1 (row 0 is a00 e_0 and is
+// written by the input split), output columns 1..rows-1 of G.
+int leg_make_split_problem(TcProblem *pr, const leg_plan *p, const LegSplitIn &in, int B, float2 *G, int ldg,
+                           int tn)
+{
+    return make_split(pr, p->Ah[0] + p->Kp, (size_t)p->rows * p->Kp, p->rows - 1, p->Kp, p->rowexp + 1, in, B,
+                      p->Kp, G + 1, ldg, tn);
+}
+
+int leg_gemm_split_fwd_into(leg_plan *p, int B, const LegSplitIn &in, float2 *G, int ldg, cudaStream_t st)
 {
     TcProblem pr;
-    int rc = make_problem(&pr, p->Fh, B, p->Ah, p->rows, p->Kp, p->fexp, p->rowexp, p->G, p->ldg, B, p->rows);
+    int rc = leg_make_split_problem(&pr, p, in, B, G, ldg, leg_split_choose_tn(p, B));
     if (rc) return rc;
-    return launch_tc<8, true>(pr, nullptr, 1, tiles_of(pr), p->status, p->wait_limit, st);
+    return launch_tc<6, true>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
+}
+
+int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st)
+{
+    return leg_gemm_split_fwd_into(p, B, leg_split_workspace(p), static_cast<float2 *>(p->G), p->ldg, st);
 }
 
 int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
 {
     // Gbar (double-float, B x ldg, rows valid) -> split planes B x npr
     const int npr = leg_round_up(leg_round_up(p->rows, 8), LEG_KPAD);
-    split_rows_kernel<float2><<<B, 256, 0, st>>>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows, npr,
-                                                 p->Fh[0], p->Fh[1], p->Fh[2], p->fexp);
+    const LegSplitIn in = leg_split_workspace(p);
+    split_rows_kernel<float2><<<B, SPLIT_THREADS, 0, st>>>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows, npr, in,
+                                                 nullptr, 0, 0.0);
     LEG_LAUNCH_CHECK("split_rows_kernel (adjoint)");
-    TcProblem pr;
-    int rc = make_problem(&pr, p->Fh, B, p->AhT, p->K, npr, p->fexp, p->colexp, df, p->K, B, p->K);
+    int pairs = 0;
+    int rc = max_pairs(&pairs);
     if (rc) return rc;
-    return launch_tc<8, false>(pr, nullptr, 1, tiles_of(pr), p->status, p->wait_limit, st);
+    TcProblem pr;
+    rc = make_split(&pr, p->AhT[0], (size_t)p->K * npr, p->K, npr, p->colexp, in, B, npr, df, p->K,
+                    p->tn ? p->tn : choose_tn(ceil_div(p->K, PAIR_M), B, npr / TILE_K, pairs));
+    if (rc) return rc;
+    return launch_tc<6, false>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
 }
 
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
@@ -559,38 +886,34 @@ int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_
 
 int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st)
 {
-    TcProblem pr;
-    int rc;
-    if ((rc = make_map(&pr.x[0], p->Fbf, p->Kp, B, p->Kp, true))) return rc;
-    if ((rc = make_map(&pr.w[0], p->Abf, p->Kp, p->rows, p->Kp, true))) return rc;
-    pr.x[1] = pr.x[2] = pr.x[0];
-    pr.w[1] = pr.w[2] = pr.w[0];
-    pr.xexp = pr.wexp = nullptr;
-    pr.out = p->G;
-    pr.ldo = p->ldg;
-    pr.B = B;
-    pr.rows = p->rows;
-    pr.nkb = p->Kp / TILE_K;
-    pr.ntj = (p->rows + TILE_N - 1) / TILE_N;
-    pr.tile0 = 0;
-    return launch_tc<1, false>(pr, nullptr, 1, tiles_of(pr), p->status, p->wait_limit, st);
-}
-
-// Variants of the split forward launchers that take their buffers explicitly
-// (used by leg_forward_noalloc, whose buffers live in a static device array).
-int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, __half *const planes[3], int *fexp,
-                                 cudaStream_t st)
-{
-    split_rows_kernel<float><<<B, 256, 0, st>>>(f, p->K, p->K, p->Kp, planes[0], planes[1], planes[2], fexp);
-    LEG_LAUNCH_CHECK("split_rows_kernel");
-    return LEG_OK;
-}
-
-int leg_gemm_split_fwd_into(leg_plan *p, int B, __half *const planes[3], const int *fexp, float2 *G, int ldg,
-                            cudaStream_t st)
-{
-    TcProblem pr;
-    int rc = make_problem(&pr, planes, B, p->Ah, p->rows, p->Kp, fexp, p->rowexp, G, ldg, B, p->rows);
+    int pairs = 0;
+    int rc = max_pairs(&pairs);
     if (rc) return rc;
-    return launch_tc<8, true>(pr, nullptr, 1, tiles_of(pr), p->status, p->wait_limit, st);
+    const int tn = p->tn ? p->tn : choose_tn(ceil_div(p->rows, PAIR_M), B, p->Kp / TILE_K, pairs);
+    TcProblem pr;
+    memset(&pr, 0, sizeof(pr));
+    if ((rc = make_map(&pr.a, p->Abf, p->Kp, p->rows, p->Kp, 1, (size_t)p->rows * p->Kp, true, CTA_M))) return rc;
+    if ((rc = make_map(&pr.f, p->Fbf, p->Kp, B, p->Kp, 1, (size_t)B * p->Kp, true, tn / 2))) return rc;
+    finish_problem(&pr, nullptr, nullptr, p->G, p->ldg, p->rows, B, p->Kp, tn);
+    return launch_tc<1, false>(pr, nullptr, 1, tiles_of(pr), tn, p->status, p->wait_limit, st);
+}
+
+// ---------------------------------------------------------------- grouped (ragged) launches
+int leg_split_problem_tiles(const TcProblem &pr) { return tiles_of(pr); }
+
+int leg_gemm_split_grouped(const TcProblem *d_probs, int nprob, int ntiles, int tn, int *status, long long limit,
+                           cudaStream_t st)
+{
+    TcProblem dummy;
+    memset(&dummy, 0, sizeof(dummy));
+    return launch_tc<6, true>(dummy, d_probs, nprob, ntiles, tn, status, limit, st);
+}
+
+int leg_split_ragged(const float *f_packed, const long long *in_off, const int *bucket, const int *row,
+                     const LegRaggedBucket *bk, int count, cudaStream_t st)
+{
+    if (count == 0) return LEG_OK;
+    split_ragged_kernel<<<count, SPLIT_THREADS, 0, st>>>(f_packed, in_off, bucket, row, bk);
+    LEG_LAUNCH_CHECK("split_ragged_kernel");
+    return LEG_OK;
 }

@@ -51,6 +51,12 @@ constexpr int LEG_MAX_K = 16385;
 // residual slices carry weights 2^-7 and 2^-14 (LEG_SPLIT_FBITS per level).
 constexpr int LEG_SPLIT_ABITS = 16;
 constexpr int LEG_SPLIT_FBITS = 7;
+// Planes of the split-FP16 GEMM: the operator side keeps its three slices
+// A0, A1, A2s; the input side carries F0, F1, the residual r - F1 at weight
+// 2^-s, and the pre-scaled copies 2^-s F1 and 2^-s F0, so that every product
+// after A0 F0 lands in one accumulator of weight 2^-s (leg_gemm_tc.cu).
+constexpr int LEG_SPLIT_NA = 3;
+constexpr int LEG_SPLIT_NF = 5;
 
 // ---------------------------------------------------------------------------
 // Plan.
@@ -71,12 +77,15 @@ struct leg_plan {
     // FP32 copy (LEG_F32), rows x K
     float *A32 = nullptr;
     // tensor-core planes, rows x Kp, K-major
-    __half *Ah[3] = {nullptr, nullptr, nullptr};   // LEG_SPLIT_FP16: A0, A1, A2s
+    __half *Ah[3] = {nullptr, nullptr, nullptr};   // LEG_SPLIT_FP16: A0, A1, A2s, one allocation
+                                                  // (Ah[s] = Ah[0] + s rows Kp)
     __nv_bfloat16 *Abf = nullptr;                 // LEG_BF16
     int *rowexp = nullptr;                        // per-row power-of-two scale (split)
+    double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
+    int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
     // transposed split planes for the adjoint GEMM: K x Kpr (Kpr = rows padded),
     // each column k of the operator scaled by its own power of two
-    __half *AhT[3] = {nullptr, nullptr, nullptr};
+    __half *AhT[3] = {nullptr, nullptr, nullptr};   // one allocation (AhT[s] = AhT[0] + s K Kpr)
     int *colexp = nullptr;
 
     // twiddles e^{2 pi i n / M}, n = 0..M-1 (computed in FP64 on the device)
@@ -92,10 +101,46 @@ struct leg_plan {
     int ws_B = 0;
     int ldg = 0;              // row stride (elements) of G
     void *G = nullptr;        // B x ldg, type by dtype (double / float / float2)
-    __half *Fh[3] = {nullptr, nullptr, nullptr};  // split input planes B x Kp
+    __half *Fh = nullptr;     // LEG_SPLIT_NF split input planes, each ws_B x ldf
+    int ldf = 0;              // row stride of the split input planes
     __nv_bfloat16 *Fbf = nullptr;                 // bf16 input plane B x Kp
     int *fexp = nullptr;                          // per-function power-of-two scale
     void *Gbar = nullptr;     // backward: B x ldg (FP64 for LEG_F64, FP32 otherwise)
+};
+
+// Split input planes of a batch: LEG_SPLIT_NF FP16 planes of B rows with row
+// stride ld; plane s starts at base + s * pstride.
+struct LegSplitIn {
+    __half *base;
+    size_t pstride;   // elements between consecutive planes
+    int ld;           // row stride (elements), a multiple of LEG_KPAD
+    int *fexp;        // per-row power-of-two scales
+};
+
+// One GEMM problem of the tcgen05 kernel (leg_gemm_tc.cu):
+//   out[b * ldo + j] = 2^(aexp[j] + fexp[b]) sum_k A[j, k] F[b, k],  j < rows, b < B,
+// operator rows on the MMA's M side (256 per CTA pair), functions on its N
+// side (tn per pair tile), both given as FP16/BF16 planes through TMA maps.
+struct TcProblem {
+    CUtensorMap a;           // operator planes (planes x rows x Kp), one 3-D map
+    CUtensorMap f;           // input planes    (planes x B x Kp), one 3-D map
+    const int *aexp;         // per-row power-of-two scales of A (or null)
+    const int *fexp;         // per-function scales of F (or null)
+    void *out;               // float2 (double-float) or float, row stride ldo
+    int ldo, rows, B;
+    int nkb;                 // Kp / 32
+    int tn;                  // functions per pair tile (multiple of 16, <= 256)
+    int ntm, ntn;            // tiles along rows (256 each) and along functions (tn each)
+    int tile0;               // first global tile index of this problem (grouped launches)
+};
+
+// Device descriptor of one bucket of a ragged batch (input-split targets).
+struct LegRaggedBucket {
+    LegSplitIn in;       // B_b x Kp split planes
+    float2 *G;           // B_b x ldg double-float G (row 0 written by the split)
+    int ldg;
+    double a00;
+    int K, Kp;
 };
 
 // ---------------------------------------------------------------------------
@@ -126,18 +171,40 @@ int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, c
 int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B, cudaStream_t st);
 int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, int B, cudaStream_t st);
 
+// register-tiled transforms (leg_dct16.cu), H = 2^log2h with 6 <= log2h <= 13;
+// dtype LEG_F64 (FP64 G, c) or LEG_SPLIT_FP16 (double-float G, FP32 c)
+int leg_dct16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
+                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
+int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
+                      cudaStream_t st);
+
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,
                 cudaStream_t st);
 
 // split-FP16 tensor-core path (leg_gemm_tc.cu)
+LegSplitIn leg_split_workspace(const leg_plan *p);
 int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st);
 int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st);
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st);
 int leg_build_split_transposed(leg_plan *p);
-int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, __half *const planes[3], int *fexp,
-                                 cudaStream_t st);
-int leg_gemm_split_fwd_into(leg_plan *p, int B, __half *const planes[3], const int *fexp, float2 *G, int ldg,
-                            cudaStream_t st);
+int leg_make_split_problem(TcProblem *pr, const leg_plan *p, const LegSplitIn &in, int B, float2 *G, int ldg,
+                           int tn);
+int leg_split_problem_tiles(const TcProblem &pr);
+int leg_gemm_split_grouped(const TcProblem *d_probs, int nprob, int ntiles, int tn, int *status, long long limit,
+                           cudaStream_t st);
+int leg_split_ragged(const float *f_packed, const long long *in_off, const int *bucket, const int *row,
+                     const LegRaggedBucket *bk, int count, cudaStream_t st);
+int leg_fft_forward_ragged(const leg_plan *p, const void *G, int ldg, float *c_packed, int B, const int *rowfn,
+                           const long long *out_off, const int *n_out, cudaStream_t st);
+int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const LegSplitIn &in, float2 *G,
+                                 int ldg, cudaStream_t st);
+int leg_gemm_split_fwd_into(leg_plan *p, int B, const LegSplitIn &in, float2 *G, int ldg, cudaStream_t st);
+// functions per pair tile for a forward of B functions (plan override, else the wave-count rule)
+int leg_split_choose_tn(const leg_plan *p, int B);
+// resident CTA pairs of the tensor-core GEMM on the current device; estimated
+// cycles of the busiest pair for ntm row tiles x B functions of K-depth nkb
+int leg_split_max_pairs(int *pairs);
+long long leg_split_tile_cost(int tn, int ntm, int B, int nkb, int pairs);

@@ -72,12 +72,13 @@ extern "C" int leg_forward_noalloc(leg_plan_t p, const float *f, float *c, int B
     if (dev != p->device)
         return leg_set_error(LEG_ERR_INVALID_ARG, "current device differs from the plan's device");
 
-    // scratch layout: three input planes (B x Kp FP16), per-function scales, G (B x ldg double-float)
+    // scratch layout: the split input planes (LEG_SPLIT_NF x B x Kp FP16),
+    // per-function scales, G (B x ldg double-float)
     const int ldg = leg_round_up(leg_round_up(p->rows, 8), LEG_KPAD);
     const size_t plane = align256(sizeof(__half) * (size_t)B * p->Kp);
     const size_t exps = align256(sizeof(int) * (size_t)B);
     const size_t gbytes = align256(sizeof(float2) * (size_t)B * ldg);
-    const size_t need = 3 * plane + exps + gbytes;
+    const size_t need = LEG_SPLIT_NF * plane + exps + gbytes;
     if (need > LEG_NOALLOC_SCRATCH_BYTES)
         return leg_set_error(LEG_ERR_INVALID_ARG,
                              "leg_forward_noalloc: this batch needs " + std::to_string(need) +
@@ -86,12 +87,14 @@ extern "C" int leg_forward_noalloc(leg_plan_t p, const float *f, float *c, int B
     unsigned char *base = nullptr;
     int rc = scratch_address(dev, &base);
     if (rc) return rc;
-    __half *planes[3] = {reinterpret_cast<__half *>(base), reinterpret_cast<__half *>(base + plane),
-                         reinterpret_cast<__half *>(base + 2 * plane)};
-    int *fexp = reinterpret_cast<int *>(base + 3 * plane);
-    float2 *G = reinterpret_cast<float2 *>(base + 3 * plane + exps);
+    LegSplitIn in;
+    in.base = reinterpret_cast<__half *>(base);
+    in.pstride = plane / sizeof(__half);
+    in.ld = p->Kp;
+    in.fexp = reinterpret_cast<int *>(base + LEG_SPLIT_NF * plane);
+    float2 *G = reinterpret_cast<float2 *>(base + LEG_SPLIT_NF * plane + exps);
 
-    if ((rc = leg_split_prepare_input_into(p, f, B, planes, fexp, st))) return rc;
-    if ((rc = leg_gemm_split_fwd_into(p, B, planes, fexp, G, ldg, st))) return rc;
+    if ((rc = leg_split_prepare_input_into(p, f, B, in, G, ldg, st))) return rc;
+    if ((rc = leg_gemm_split_fwd_into(p, B, in, G, ldg, st))) return rc;
     return leg_fft_forward(p, G, ldg, c, B, st);
 }

@@ -302,8 +302,10 @@ int leg_build_planes(leg_plan *p)
         LEG_TRY_CLEAN(cudaMalloc(&p->Abf, sizeof(__nv_bfloat16) * (size_t)rows * p->Kp));
         plane_bf16_kernel<<<rows, 256>>>(p->A64, K, p->Kp, p->Abf);
     } else if (p->dtype == LEG_SPLIT_FP16) {
-        for (int s = 0; s < 3; ++s)
-            LEG_TRY_CLEAN(cudaMalloc(&p->Ah[s], sizeof(__half) * (size_t)rows * p->Kp));
+        const size_t plane = (size_t)rows * p->Kp;
+        LEG_TRY_CLEAN(cudaMalloc(&p->Ah[0], sizeof(__half) * 3 * plane));
+        p->Ah[1] = p->Ah[0] + plane;
+        p->Ah[2] = p->Ah[0] + 2 * plane;
         LEG_TRY_CLEAN(cudaMalloc(&p->rowexp, sizeof(int) * rows));
         plane_split_kernel<<<rows, 256>>>(p->A64, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp);
         LEG_TRY_CLEAN(cudaGetLastError());
@@ -315,6 +317,8 @@ int leg_build_planes(leg_plan *p)
     }
     LEG_TRY_CLEAN(cudaGetLastError());
     LEG_TRY_CLEAN(cudaDeviceSynchronize());
+    // row 0 (y = 0: every quadrature point is x = 1, the node k = 0) is a00 e_0
+    if (p->dtype == LEG_SPLIT_FP16) LEG_TRY_CLEAN(cudaMemcpy(&p->a00, p->A64, sizeof(double), cudaMemcpyDeviceToHost));
 #undef LEG_TRY_CLEAN
     return LEG_OK;
 }

@@ -95,3 +95,53 @@ def ragged_spec(count: int, rng: np.random.Generator, Nmin: int = 32, Nmax: int 
     n = np.exp(rng.uniform(np.log(Nmin), np.log(Nmax), count))
     n = np.clip(np.floor(n).astype(np.int64), Nmin, Nmax)
     return fam.astype(np.int32), par, n
+
+
+def bucket_of(n: int) -> int:
+    """Size bucket of a function needing n coefficients: next power of two >= n."""
+    return 1 << int(np.ceil(np.log2(max(int(n), 1))))
+
+
+def bucket_sizes(Nb: int):
+    """(N, M, K, Q) of the plan of bucket Nb: M = 4N, K = min(2N, 1024) + 1,
+    Q = max(32, N/8) Gauss nodes per y-point."""
+    return Nb, 4 * Nb, min(2 * Nb, 1024) + 1, max(32, Nb // 8)
+
+
+def ragged_layout(fam, par, n, rng: np.random.Generator):
+    """Packed layout of a ragged batch.
+
+    Returns a dict with the bucket list (sorted N_b), per-function bucket
+    index, K, input/output offsets, and the Chebyshev coefficients (FP64,
+    g_m rho^m, g_m ~ N(0,1)) of the functions of that family.
+    """
+    Nb = np.array([bucket_of(v) for v in n])
+    buckets = sorted(set(Nb.tolist()))
+    bidx = np.array([buckets.index(v) for v in Nb], dtype=np.int32)
+    K = np.array([bucket_sizes(v)[2] for v in Nb], dtype=np.int32)
+    in_off = np.concatenate([[0], np.cumsum(K)[:-1]]).astype(np.int64)
+    out_off = np.concatenate([[0], np.cumsum(n)[:-1]]).astype(np.int64)
+    coef_off = np.zeros(len(n), dtype=np.int64)
+    coefs = []
+    pos = 0
+    for i in range(len(n)):
+        if fam[i] == 2:
+            coef_off[i] = pos
+            g = rng.standard_normal(K[i]) * par[i] ** np.arange(K[i])
+            coefs.append(g)
+            pos += K[i]
+    coef = np.concatenate(coefs) if coefs else np.zeros(1)
+    return dict(buckets=buckets, bidx=bidx, K=K, in_off=in_off, out_off=out_off, coef_off=coef_off,
+                coef=coef, n_in=int(K.sum()), n_out=int(np.sum(n)))
+
+
+def closed_form_samples(fam: int, par: float, K: int, coef=None) -> np.ndarray:
+    """FP64 values of one closed-form function at its K CL nodes (host reference)."""
+    k = np.arange(K)
+    omx = 2.0 * np.sin(np.pi * k / (2.0 * (K - 1))) ** 2
+    x = np.cos(np.pi * k / (K - 1))
+    if fam == 0:
+        return ((1.0 - par) ** 2 + 2.0 * par * omx) ** -0.5
+    if fam == 1:
+        return np.exp(par * x)
+    return chebyshev_values(coef)[0]
