@@ -180,9 +180,37 @@ def reference_arm(args, rank, world):
 # ------------------------------------------------------------------ GPU arm
 PATHS = {"split_fp16": 3, "f32": 1, "bf16": 2, "f64": 0}
 DTYPE_STR = {
-    "split_fp16": "f16x3 split (8 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
+    "split_fp16": "f16 split (8 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
     "f32": "f32", "bf16": "bf16 (f32 accum) + f32 FFT", "f64": "f64",
 }
+
+
+# Peak arithmetic rates of the FFT stage (ops/s in units of 1e12), from unit
+# counts and clocks: 152 SMs x 128 FP32 lanes x 2.07 GHz (one FP32 add, mul or
+# FMA per lane per cycle); FP64: the GB300's nominal 1.25 TFLOP/s dense.
+ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
+
+# DRAM bytes (read + write) per launch measured by ncu for the current kernels
+# (profiles/*.md name the captures); keyed by (stage, path, workload).
+TRAFFIC = {
+    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 57383424,   # tc_gemm_pair_split_fp16_...
+    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34175488,         # dct16_forward_dfl_...
+}
+
+
+def fft_fp32_ops(M, N):
+    """FP32 operations of the double-float transform of one function (the
+    algorithmic operation count of the method's FFT stage at the precision it
+    needs): a length-H complex FFT (H = M/4) with (H/2) log2 H radix-2
+    butterflies of 4 mul + 6 add, the fold (L = M/2 values: 3.5 add + 2.5 mul
+    each), the recombination (H x 8 add + 4 mul), the scan (H add) and the
+    output (N x 1 add + 1 mul), each double-float add costing 8 FP32 operations
+    (TwoSum + trailing add) and each multiply 4 (exact product by FMA + 2 FMA)."""
+    H, L = M // 4, M // 2
+    lg = int(round(np.log2(H)))
+    adds = 3 * H * lg + 3.5 * L + 8 * H + H + N
+    muls = 2 * H * lg + 2.5 * L + 4 * H + N
+    return 8 * adds + 4 * muls
 
 
 def relerr(c, ref):
@@ -357,33 +385,56 @@ def gpu_arm(args, rank, world, local_rank):
     ref = O.coeffs_abel(N, M, O.exact_tau_points(K), f_cl=res["f_np"][:16].astype(np.float64))
     err = relerr(res["c_sample"], ref)
 
-    # ---------------- roofline of the dominant kernel
+    # ---------------- rooflines (algorithmic work per launch / CUDA-event stage time)
+    Kp = (K + 63) // 64 * 64
     flops_useful = 2.0 * B * rows * K                      # per GEMM launch (distinct rows, eq. 2.12)
     products = {"split_fp16": 8, "bf16": 1, "f32": 1, "f64": 1}[args.path]
+    gemm_rows = rows - 1 if args.path == "split_fp16" else rows   # split: row 0 is a00 e_0, done by the split
+    executed = products * 2.0 * B * gemm_rows * Kp
     fft_bytes = B * rows * (8 if args.path in ("split_fp16", "f64") else 4) + B * N * (8 if args.path == "f64" else 4)
-    prep_bytes = B * K * 4 + 3 * B * ((K + 63) // 64 * 64) * 2 + B * 4
+    nplanes = 7 if args.path == "split_fp16" else 1
+    prep_bytes = B * K * 4 + nplanes * B * Kp * 2 + B * 4 + (B * 8 if args.path == "split_fp16" else 0)
+    peak_tensor = peaks.get("bf16_tflops", 1899.1)
+    gemm_roof = {"kernel": "tc_gemm_kernel (Abel GEMM)", "bound": "tensor",
+                 "achieved": flops_useful / (gemm_ms / 1e3) / 1e12, "peak": peak_tensor, "unit": "TFLOP/s",
+                 "flops_per_launch": flops_useful, "executed_flops_per_launch": executed,
+                 "executed_tflops": executed / (gemm_ms / 1e3) / 1e12,
+                 "traffic": TRAFFIC.get(("abel_gemm", args.path, name)),
+                 "peak_source": "%s bf16_tflops (fp16 dense rate equals bf16)" % peak_src}
+    gemm_roof["frac"] = gemm_roof["achieved"] / peak_tensor
+    hbm = peaks.get("hbm_gbs", 6696.2)
+    fft_hbm = fft_bytes / (fft_ms / 1e3) / 1e9
+    if args.path in ("split_fp16", "f64"):
+        # double-float (or FP64) transform: bound by FP32 (FP64) arithmetic, see fft_fp32_ops
+        ops = fft_fp32_ops(M, N) * B
+        peak_alu = ALU_PEAK_TOPS["f64" if args.path == "f64" else "f32"]
+        fft_roof = {"kernel": "dct16_forward_kernel (FFT stage)", "bound": "alu",
+                    "achieved": ops / (fft_ms / 1e3) / 1e12, "peak": peak_alu, "unit": "Tops/s",
+                    "ops_per_launch": ops, "hbm_gbs": fft_hbm, "hbm_frac": fft_hbm / hbm,
+                    "traffic": TRAFFIC.get(("fft", args.path, name)),
+                    "peak_source": "derived: SMs x lanes x max SM clock (see DESIGN.md)"}
+        fft_roof["frac"] = fft_roof["achieved"] / peak_alu
+    else:
+        fft_roof = {"kernel": "fft_forward_kernel (FFT stage)", "bound": "hbm", "achieved": fft_hbm, "peak": hbm,
+                    "unit": "GB/s", "frac": fft_hbm / hbm, "bytes_per_launch": fft_bytes,
+                    "traffic": TRAFFIC.get(("fft", args.path, name)), "peak_source": "%s hbm_gbs" % peak_src}
     kernels = {"abel_gemm": gemm_ms, "fft": fft_ms, "input_split": prep_ms}
     dom = max(kernels, key=kernels.get)
-    peak_tensor = peaks.get("bf16_tflops", 1899.1)
-    if dom == "abel_gemm" and args.path in ("split_fp16", "bf16"):
-        achieved = flops_useful / (gemm_ms / 1e3) / 1e12
-        roof = {"kernel": "tc_gemm_kernel (Abel GEMM)", "bound": "tensor", "achieved": achieved,
-                "peak": peak_tensor, "unit": "TFLOP/s", "frac": achieved / peak_tensor, "traffic": None,
-                "flops_per_launch": flops_useful, "executed_flops_per_launch": products * 2.0 * B * rows *
-                ((K + 63) // 64 * 64), "peak_source": "%s bf16_tflops (fp16 dense rate equals bf16)" % peak_src}
+    if dom == "fft":
+        roof = fft_roof
+    elif dom == "abel_gemm" and args.path in ("split_fp16", "bf16"):
+        roof = gemm_roof
     else:
-        nm = dom
-        by = {"fft": fft_bytes, "input_split": prep_bytes, "abel_gemm": B * K * 4 + rows * K * 4 + B * rows * 4}[nm]
-        achieved = by / (kernels[nm] / 1e3) / 1e9
-        roof = {"kernel": nm, "bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6696.2),
-                "unit": "GB/s", "frac": achieved / peaks.get("hbm_gbs", 6696.2), "traffic": None,
-                "bytes_per_launch": by, "peak_source": "%s hbm_gbs" % peak_src}
+        by = {"input_split": prep_bytes, "abel_gemm": B * K * 4 + rows * K * 4 + B * rows * 4}[dom]
+        achieved = by / (kernels[dom] / 1e3) / 1e9
+        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm, "traffic": None, "bytes_per_launch": by, "peak_source": "%s hbm_gbs" % peak_src}
     stages = {
         "input_split": {"ms": prep_ms, "bytes": prep_bytes,
                         "gbs": prep_bytes / (prep_ms / 1e3) / 1e9 if prep_ms > 0 else None},
-        "abel_gemm": {"ms": gemm_ms, "useful_tflops": flops_useful / (gemm_ms / 1e3) / 1e12,
-                      "executed_tflops": products * flops_useful / (gemm_ms / 1e3) / 1e12},
-        "fft": {"ms": fft_ms, "bytes": fft_bytes, "gbs": fft_bytes / (fft_ms / 1e3) / 1e9},
+        "abel_gemm": dict(gemm_roof, ms=gemm_ms) if args.path in ("split_fp16", "bf16") else
+                     {"ms": gemm_ms, "useful_tflops": flops_useful / (gemm_ms / 1e3) / 1e12},
+        "fft": dict(fft_roof, ms=fft_ms),
     }
 
     extras = {}

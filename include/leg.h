@@ -234,9 +234,10 @@ LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
 /*
  * leg_plan_set_tile -- width of the output tile of the tensor-core Abel GEMM
  * (LEG_SPLIT_FP16 forward and adjoint, LEG_BF16): tn functions per CTA-pair
- * tile of 256 operator rows, a multiple of 16 in 16..256; 0 (the default)
- * lets the library pick tn per call from the batch size, the rows and the
- * number of resident CTA pairs (fewest MMA cycles on the busiest pair).
+ * tile of 256 operator rows, a multiple of 16 in 16..128 (LEG_BF16: 16..256);
+ * 0 (the default) lets the library pick tn per call from the batch size,
+ * the rows and the number of resident CTA pairs (fewest MMA cycles on the
+ * busiest pair).
  * A tuning knob only: results do not depend on it.
  */
 LEG_API int leg_plan_set_tile(leg_plan_t plan, int tn);
@@ -261,7 +262,7 @@ LEG_API int leg_plan_tile_info(leg_plan_t plan, int B, int *tn, int *pairs, int 
  * The intermediate buffers (input slices, per-function scales, the Abel
  * GEMM result) come from one static device array of 64 MiB in the library,
  * which every GPU that loads the library keeps reserved until process exit.
- * A batch needing more scratch than that (about B*(10*Kp + 8*Mr) bytes, Kp = K
+ * A batch needing more scratch than that (about B*(14*Kp + 8*Mr) bytes, Kp = K
  * rounded up to 64, Mr = M/2+1 rounded up to 64) is rejected with
  * LEG_ERR_INVALID_ARG and a message stating the sizes.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that

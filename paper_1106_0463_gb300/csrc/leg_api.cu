@@ -362,8 +362,10 @@ extern "C" int leg_plan_set_wait_limit(leg_plan_t p, long long cycles)
 extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
 {
     if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
-    if (tn != 0 && (tn < 16 || tn > 256 || tn % 16 != 0))
-        return leg_set_error(LEG_ERR_INVALID_ARG, "tile width must be 0 or a multiple of 16 in 16..256");
+    const int maxtn = (p->dtype == LEG_BF16) ? 256 : 128;
+    if (tn != 0 && (tn < 16 || tn > maxtn || tn % 16 != 0))
+        return leg_set_error(LEG_ERR_INVALID_ARG, "tile width must be 0 or a multiple of 16 in 16.." +
+                                                      std::to_string(maxtn) + " for this plan");
     p->tn = tn;
     return LEG_OK;
 }

@@ -8,26 +8,28 @@
 // rounding noise in G into errors ~ (2N/sqrt(M)) times larger in c_n; FP32
 // accumulation of the whole product therefore cannot meet 1e-6.
 //
-// LEG_SPLIT_FP16 (three-slice split, six products, two accumulators):
+// LEG_SPLIT_FP16 (three-slice split, eight products, three accumulators):
 //   each operand row is scaled by a power of two (the operator by its L1
-//   norm, the input by its max-norm) and split into FP16 slices, s = 7:
+//   norm, the input by its max-norm) and split into FP16 slices,
+//   s = LEG_SPLIT_FBITS = 7, LEG_SPLIT_ABITS = 16:
 //     a = A0 + 2^-s A1 + 2^-2s A2s,     A0 on a 2^-16 grid,
-//     f = F0 + 2^-s r,  r = F1 + (r - F1),   F0 on a 2^-s grid.
-//   Accumulator 0 takes A0 F0: the products lie on a 2^-23 grid and every
-//   partial sum stays below 2, so it is EXACT in FP32 whatever the order or
-//   truncation of the tensor core's additions.  Accumulator 1 (weight 2^-s)
-//   takes A1 F0 + A0 F1 + A0 (r - F1) + A1 (2^-s F1) + A2s (2^-s F0): the
-//   terms of weight 2^-2s reach it through input planes pre-scaled by 2^-s
-//   (exact for F0; below the FP16 normal range for F1 and r - F1 they keep an
-//   absolute 2^-25, which the L1-normalised rows bound by 2^-32 in G).  The
-//   dropped terms A2s F1, A1 (r - F1) and A2s (r - F1) have weight <= 2^-3s
-//   times slices below 2^-10.
-//   Accumulator 0 runs over the whole K range of a tile (it is exact).
-//   Accumulator 1 is split into chunks of 256 K: after each chunk the
-//   epilogue warps add it into registers and release its TMEM buffer, which
-//   bounds the tensor core's truncation error of accumulator 1 (it grows
-//   with the chunk's length and magnitude).  The epilogue forms
-//   G = 2^(e_j + e_b) (acc0 + 2^-s acc1) as a double-float pair.
+//     f = F0 + 2^-s r,  r = F1 + (r - F1),   F0 on a 2^-7 grid.
+//   acc0 takes A0 F0 over the whole tile: the products lie on a 2^-23 grid
+//   and every partial sum stays below 2, so it is EXACT in FP32 whatever the
+//   order or truncation of the tensor core's additions.
+//   acc1 (weight 2^-s) takes the two largest correction terms A1 F0 + A0 F1
+//   in K chunks of 128: after each chunk the epilogue warps add it into
+//   registers and release its TMEM buffer (two buffers), which bounds the
+//   tensor core's truncating FP32 accumulation (its error grows with the
+//   chunk's length and magnitude).
+//   acc2 (weight 2^-s as well, whole tile) takes the small terms through input
+//   planes pre-scaled by 2^-s or 2^-2s: A0 (r - F1), A1 2^-s F1, A2s 2^-s F0
+//   (weight 2^-2s) and A2s 2^-2s F1, A1 2^-s (r - F1) (weight 2^-3s); below
+//   the FP16 normal range the pre-scaled planes keep an absolute 2^-25, which
+//   the L1-normalised rows bound by 2^-32 in G.  Only A2s (r - F1) (weight
+//   2^-4s) is dropped.
+//   The epilogue forms G = 2^(e_j + e_b) (acc0 + 2^-s (acc1 + acc2)) as a
+//   double-float pair.
 // LEG_BF16: one BF16 product, one accumulator (FP32 G).
 //
 // Kernel: persistent, CTA pairs (cluster of 2, tcgen05 cta_group::2).  A pair
@@ -68,9 +70,9 @@ namespace {
 constexpr int CTA_M = 128;                          // operator rows per CTA (TMEM lanes)
 constexpr int PAIR_M = 2 * CTA_M;                   // MMA M of a CTA pair
 constexpr int TILE_K = 32;                          // K per stage: 64-byte FP16 rows
-constexpr int MAX_TN = 256;                         // functions per pair tile, at most
+constexpr int MAX_TN = 256;                         // functions per pair tile, at most (BF16)
 constexpr int ATILE_BYTES = CTA_M * TILE_K * 2;     // 8 KB per operator plane
-constexpr int CHUNK_KB = 8;                         // K blocks per accumulation chunk of acc1
+constexpr int CHUNK_KB = 4;                         // K blocks per accumulation chunk of acc1
 constexpr int MAX_STAGES = 8;
 constexpr int EPI_WARPS = 16;                       // four per TMEM lane quadrant
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -80,7 +82,7 @@ constexpr size_t SMEM_STATIC_RESERVE = 1024 + 512;  // 1 KB alignment slack + st
 constexpr long long DRAIN_LIMIT = 4000000000LL;     // cycles, teardown waits
 
 template <int NPROD> struct TcCfg;
-template <> struct TcCfg<6> {
+template <> struct TcCfg<8> {
     static constexpr int NA = LEG_SPLIT_NA, NF = LEG_SPLIT_NF, BF16 = 0;
 };
 template <> struct TcCfg<1> {
@@ -105,10 +107,13 @@ constexpr int stages_for(int tn)
     return s > MAX_STAGES ? MAX_STAGES : s;
 }
 
-// TMEM columns: acc0 [0, tn) for the whole tile; acc1 in one or two chunk
-// buffers: [tn (1 + b), tn (2 + b)) when three tn-wide regions fit, else [256, 256 + tn).
-__host__ __device__ constexpr int acc1_buffers(int tn) { return 3 * tn <= (int)TMEM_COLS ? 2 : 1; }
-__device__ __forceinline__ uint32_t acc1_col(int tn, int b) { return acc1_buffers(tn) == 2 ? (uint32_t)(tn * (1 + b)) : 256u; }
+// Maximum tile width of a launch: the split path keeps four tn-wide TMEM
+// regions (acc0, acc2, two acc1 chunk buffers), the BF16 path one.
+template <int NPROD> __host__ __device__ constexpr int max_tn() { return NPROD > 1 ? 128 : 256; }
+
+// TMEM columns of the split path: acc0 [0, tn), acc2 [tn, 2tn) for the whole
+// tile; acc1 chunk buffer b in [(2 + b) tn, (3 + b) tn).
+__device__ __forceinline__ uint32_t acc1_col(int tn, int b) { return (uint32_t)(tn * (2 + b)); }
 
 // Pair tile t of a launch: its problem, first operator row j0, first function b0.
 // Row tiles vary fastest, so concurrent pairs share their input tiles in L2.
@@ -143,7 +148,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long l
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// tn: functions per pair tile (multiple of 16, <= 256; every problem of the
+// tn: functions per pair tile (multiple of 16, <= max_tn; every problem of the
 // launch uses it); stages: pipeline depth (<= MAX_STAGES, fits stage_bytes(tn)).
 template <int NPROD, bool OUT_DF>
 __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_constant__ TcProblem single,
@@ -155,21 +160,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     constexpr int NA = Cfg::NA, NF = Cfg::NF;
     const int FT = ftile_bytes(tn);
     const int SB = stage_bytes<NPROD>(tn);
-    const int nbuf = acc1_buffers(tn);
 
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));   // swizzle atoms need 512 B
-    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];    // this CTA's copies of a stage landed
-    __shared__ __align__(8) uint64_t peer_bar[MAX_STAGES];    // (even CTA) the odd CTA's copies landed
+    __shared__ __align__(8) uint64_t full_bar[MAX_STAGES];    // (even CTA) both CTAs' copies of a stage landed
     __shared__ __align__(8) uint64_t empty_bar[MAX_STAGES];   // the pair MMAs reading a stage completed
     __shared__ __align__(8) uint64_t chunk_full[2];           // an acc1 chunk is final
     __shared__ __align__(8) uint64_t chunk_empty[2];          // (even CTA) both epilogues have read it
-    __shared__ __align__(8) uint64_t acc_full;                // acc0 of a tile is final
-    __shared__ __align__(8) uint64_t acc_empty;               // (even CTA) both epilogues have read it
+    __shared__ __align__(8) uint64_t acc_full;                // acc0 (and acc2) of a tile are final
+    __shared__ __align__(8) uint64_t acc_empty;               // (even CTA) both epilogues have read them
     __shared__ __align__(8) uint64_t drain_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int s_abort;
+    __shared__ volatile uint32_t s_peer_issued;               // (even CTA) copies issued by the odd CTA
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t rank = sm100::cluster_ctarank();   // 0: MMA issuer of the pair
@@ -178,7 +182,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     if (threadIdx.x == 0) {
         for (int s = 0; s < MAX_STAGES; ++s) {
             sm100::mbar_init(&full_bar[s], 1);
-            sm100::mbar_init(&peer_bar[s], 1);
             sm100::mbar_init(&empty_bar[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         sm100::mbar_init(&acc_empty, 2 * EPI_WARPS);
         sm100::mbar_init(&drain_bar, 1);
         s_abort = 0;
+        s_peer_issued = 0;
         sm100::fence_mbar_init();
         if (!multi) {
             sm100::prefetch_tmap(&single.a);
@@ -209,14 +213,18 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         s_abort = 1;
         sm100::st_cluster_u32(peer_abort, 1u);
     };
+    const uint32_t bytes = NA * ATILE_BYTES + NF * FT;   // one CTA's copies per stage
+    uint32_t issued = 0;                                  // producer: stages issued (lane 0 of warp 0)
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer warp (both CTAs)
+        // Both CTAs' copies of a stage complete on the even CTA's full barrier,
+        // which the even producer arms with both CTAs' byte counts.
         const bool leader = sm100::elect_one();
-        uint32_t s = 0, ph = 0, issued = 0;   // stage ring position, continues across tiles
+        const uint32_t full0 = sm100::mapa_shared(sm100::smem_u32(&full_bar[0]), 0u);
+        uint32_t s = 0, ph = 0;
         bool ok = true;
         const int half = tn >> 1;
-        const uint32_t bytes = NA * ATILE_BYTES + NF * FT;
         for (int t = cid; ok && t < ntiles; t += ncl) {
             int j0, b0;
             const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
@@ -227,15 +235,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     break;
                 }
                 if (leader) {
-                    // one box per plane (third coordinate) of each operand
                     unsigned char *st = smem + s * SB;
-                    sm100::mbar_arrive_expect_tx(&full_bar[s], bytes);
+                    const uint32_t fb = full0 + 8u * s;
+                    if (rank == 0) sm100::mbar_arrive_expect_tx(&full_bar[s], 2 * bytes);
 #pragma unroll
                     for (int p = 0; p < NA; ++p)
-                        sm100::tma_load_3d(st + p * ATILE_BYTES, &pr.a, &full_bar[s], kb * TILE_K, arow, p);
+                        sm100::tma_load_3d_pair(st + p * ATILE_BYTES, &pr.a, fb, kb * TILE_K, arow, p);
 #pragma unroll
                     for (int p = 0; p < NF; ++p)
-                        sm100::tma_load_3d(st + NA * ATILE_BYTES + p * FT, &pr.f, &full_bar[s], kb * TILE_K, frow, p);
+                        sm100::tma_load_3d_pair(st + NA * ATILE_BYTES + p * FT, &pr.f, fb, kb * TILE_K, frow, p);
                 }
                 __syncwarp();
                 ++issued;
@@ -245,16 +253,14 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                 }
             }
         }
-        if (lane == 0) {
-            if (!ok) fail();
-            // drain: the last copy issued into every stage has landed before exit
-            const uint32_t first = issued > (uint32_t)stages ? issued - stages : 0;
-            for (uint32_t i = first; i < issued; ++i)
-                sm100::mbar_wait(&full_bar[i % stages], (i / stages) & 1, DRAIN_LIMIT);
-        }
+        if (!ok && lane == 0) fail();
+        if (lane == 0 && rank == 1)   // the even CTA reconciles and drains both CTAs' copies
+            sm100::st_cluster_u32(sm100::mapa_shared(sm100::smem_u32(const_cast<uint32_t *>(&s_peer_issued)), 0u),
+                                  issued);
     } else if (warp == 1 && rank == 0) {
         // ------------------------------------------------ MMA warp (even CTA)
         const bool leader = sm100::elect_one();
+        const int nbuf = 2;
         uint32_t s = 0, ph = 0, cc = 0;   // stage ring position, acc1 chunk counter
         bool ok = true;
         const uint32_t idesc = sm100::idesc_f16(PAIR_M, tn, Cfg::BF16);
@@ -262,16 +268,16 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         for (int t = cid; ok && t < ntiles; t += ncl, ++ti) {
             int j0, b0;
             const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
-            // acc0 of the previous tile has been read by both epilogues
+            // acc0 / acc2 of the previous tile have been read by both epilogues
             if (!warp_wait(&acc_empty, (ti & 1) ^ 1, wait_limit, &s_abort)) {
                 ok = false;
                 break;
             }
             sm100::tc_fence_after();
-            uint32_t acc1 = tmem + 256;
+            const uint32_t acc2 = tmem + (uint32_t)tn;
+            uint32_t acc1 = tmem + acc1_col(tn, 0);
             for (int kb = 0; kb < pr.nkb; ++kb) {
-                if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort) ||
-                    !warp_wait(&peer_bar[s], ph, wait_limit, &s_abort)) {
+                if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort)) {
                     ok = false;
                     break;
                 }
@@ -281,11 +287,22 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                 const uint64_t d0 = sm100::desc_k_sw64(sm100::smem_u32(smem + s * SB));
                 auto A = [&](int p, int kk) { return d0 + (uint64_t)((p * ATILE_BYTES + kk * 32) >> 4); };
                 auto F = [&](int p, int kk) { return d0 + (uint64_t)((NA * ATILE_BYTES + p * FT + kk * 32) >> 4); };
-                // acc0 (weight 1): A0 F0, accumulated over the whole tile
+                const uint32_t first = (kb == 0) ? 0u : 1u;   // first K block of the tile
                 if (leader) {
 #pragma unroll
-                    for (int kk = 0; kk < TILE_K / 16; ++kk)
-                        sm100::mma_f16_pair(tmem, A(0, kk), F(0, kk), idesc, (kb == 0 && kk == 0) ? 0u : 1u);
+                    for (int kk = 0; kk < TILE_K / 16; ++kk) {
+                        // acc0 (weight 1): A0 F0, whole tile, exact
+                        sm100::mma_f16_pair(tmem, A(0, kk), F(0, kk), idesc, (first | kk) ? 1u : 0u);
+                        if constexpr (NPROD > 1) {
+                            // acc2 (weight 2^-s): the terms of weight 2^-2s and 2^-3s through
+                            // the pre-scaled input planes, whole tile
+                            sm100::mma_f16_pair(acc2, A(0, kk), F(2, kk), idesc, (first | kk) ? 1u : 0u);   // A0 (r - F1)
+                            sm100::mma_f16_pair(acc2, A(1, kk), F(3, kk), idesc, 1u);   // A1 2^-s F1
+                            sm100::mma_f16_pair(acc2, A(2, kk), F(4, kk), idesc, 1u);   // A2s 2^-s F0
+                            sm100::mma_f16_pair(acc2, A(2, kk), F(5, kk), idesc, 1u);   // A2s 2^-2s F1
+                            sm100::mma_f16_pair(acc2, A(1, kk), F(6, kk), idesc, 1u);   // A1 2^-s (r - F1)
+                        }
+                    }
                 }
                 if constexpr (NPROD > 1) {
                     const int kc = kb % CHUNK_KB;
@@ -301,12 +318,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     if (leader) {
 #pragma unroll
                         for (int kk = 0; kk < TILE_K / 16; ++kk) {
-                            // acc1 (weight 2^-s): five products, the 2^-2s terms via pre-scaled inputs
-                            sm100::mma_f16_pair(acc1, A(1, kk), F(0, kk), idesc, (kc == 0 && kk == 0) ? 0u : 1u);
+                            // acc1 (weight 2^-s): the two largest products, in K chunks
+                            sm100::mma_f16_pair(acc1, A(1, kk), F(0, kk), idesc, (kc == 0 && kk == 0) ? 0u : 1u);  // A1 F0
                             sm100::mma_f16_pair(acc1, A(0, kk), F(1, kk), idesc, 1u);   // A0 F1
-                            sm100::mma_f16_pair(acc1, A(0, kk), F(2, kk), idesc, 1u);   // A0 (r - F1)
-                            sm100::mma_f16_pair(acc1, A(1, kk), F(3, kk), idesc, 1u);   // A1 2^-s F1
-                            sm100::mma_f16_pair(acc1, A(2, kk), F(4, kk), idesc, 1u);   // A2s 2^-s F0
                         }
                         sm100::mma_commit_pair_mc(&empty_bar[s], 0x3);
                         if (kc == CHUNK_KB - 1 || kb == pr.nkb - 1) sm100::mma_commit_pair_mc(&chunk_full[cc % nbuf], 0x3);
@@ -331,29 +345,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
             sm100::mma_commit_pair_mc(&drain_bar, 0x1);
             sm100::mbar_wait(&drain_bar, 0, DRAIN_LIMIT);
         }
-    } else if (warp == 1) {
-        // ------------------------------------------------ relay warp (odd CTA)
-        const uint32_t peer0 = sm100::mapa_shared(sm100::smem_u32(&peer_bar[0]), 0u);
-        uint32_t s = 0, ph = 0;
-        bool ok = true;
-        for (int t = cid; ok && t < ntiles; t += ncl) {
-            int j0, b0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
-            for (int kb = 0; kb < pr.nkb; ++kb) {
-                if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort)) {
-                    ok = false;
-                    break;
-                }
-                if (lane == 0) sm100::mbar_arrive_cluster(peer0 + 8u * s);
-                __syncwarp();
-                if (++s == (uint32_t)stages) {
-                    s = 0;
-                    ph ^= 1;
-                }
-            }
-        }
-        if (!ok && lane == 0) fail();
-    } else {
+    } else if (warp >= 2) {
         // ------------------------------------------------ epilogue (both CTAs)
         // Warp (quadrant q, group cg) owns TMEM lanes 32q.. (operator rows) and the
         // 16-column units cg, cg + 4, cg + 8, cg + 12 below tn (functions).
@@ -363,6 +355,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         const uint32_t chunk_empty0 = sm100::mapa_shared(sm100::smem_u32(&chunk_empty[0]), 0u);
         const uint32_t acc_empty0 = sm100::mapa_shared(sm100::smem_u32(&acc_empty), 0u);
         const int nunits = tn >> 4;
+        constexpr int MU = max_tn<NPROD>() / 64;        // units per warp, at most
         constexpr float W1 = 1.0f / (float)(1 << LEG_SPLIT_FBITS);
         uint32_t cc = 0;
         int ti = 0;
@@ -372,21 +365,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
             const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
             // per-function scales of this warp's columns: lane l holds unit m's
             // column (l & 15); fetched before the accumulators are ready
-            int fe[4] = {0, 0, 0, 0};
-            if (NPROD > 1 && pr.fexp) {
+            int fe[MU];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) {
-                    const int bi = b0 + (cg + 4 * m) * 16 + (lane & 15);
-                    if (cg + 4 * m < nunits && bi < pr.B) fe[m] = pr.fexp[bi];
-                }
+            for (int m = 0; m < MU; ++m) {
+                fe[m] = 0;
+                const int bi = b0 + (cg + 4 * m) * 16 + (lane & 15);
+                if (NPROD > 1 && pr.fexp && cg + 4 * m < nunits && bi < pr.B) fe[m] = pr.fexp[bi];
             }
-            float r1[64];
+            float r1[16 * MU];
 #pragma unroll
-            for (int i = 0; i < 64; ++i) r1[i] = 0.0f;
+            for (int i = 0; i < 16 * MU; ++i) r1[i] = 0.0f;
             if constexpr (NPROD > 1) {
                 const int nch = (pr.nkb + CHUNK_KB - 1) / CHUNK_KB;
                 for (int ch = 0; ch < nch; ++ch, ++cc) {
-                    const uint32_t b = cc % nbuf, u = cc / nbuf;
+                    const uint32_t b = cc % 2, u = cc / 2;
                     if (!warp_wait(&chunk_full[b], u & 1, wait_limit, &s_abort)) {
                         ok = false;
                         break;
@@ -395,7 +387,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     sm100::tc_fence_after();
                     const uint32_t base = lane_base + acc1_col(tn, (int)b);
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
+                    for (int m = 0; m < MU; ++m) {
                         if (cg + 4 * m < nunits) {
                             float tv[16];
                             sm100::tmem_ld_32x32b_x16(base + (uint32_t)((cg + 4 * m) * 16), tv);
@@ -420,11 +412,20 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
             const bool row_ok = j < pr.rows;
             const int ej = (row_ok && pr.aexp) ? pr.aexp[j] : 0;
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
+            for (int m = 0; m < MU; ++m) {
                 if (cg + 4 * m >= nunits) continue;
+                const uint32_t col = (uint32_t)((cg + 4 * m) * 16);
                 float tv[16];
-                sm100::tmem_ld_32x32b_x16(lane_base + (uint32_t)((cg + 4 * m) * 16), tv);
-                sm100::tmem_ld_wait();
+                sm100::tmem_ld_32x32b_x16(lane_base + col, tv);
+                if constexpr (NPROD > 1) {
+                    float t2[16];
+                    sm100::tmem_ld_32x32b_x16(lane_base + (uint32_t)tn + col, t2);
+                    sm100::tmem_ld_wait();
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) r1[16 * m + i] += t2[i];
+                } else {
+                    sm100::tmem_ld_wait();
+                }
                 const int bb = b0 + (cg + 4 * m) * 16;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     }
                 }
             }
-            // acc0 read: the MMA warp may start the next tile
+            // acc0 / acc2 read: the MMA warp may start the next tile
             sm100::tc_fence_before();
             __syncwarp();
             if (lane == 0) sm100::mbar_arrive_cluster(acc_empty0);
@@ -451,7 +452,24 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     }
     __syncwarp();
     sm100::tc_fence_before();
-    sm100::cluster_sync();
+    sm100::cluster_sync();   // every role of both CTAs has stopped issuing
+    if (rank == 0 && warp == 0 && lane == 0) {
+        // Drain both CTAs' copies.  After an abort the two producers may have
+        // issued different numbers of stages (at most `stages` apart): stages
+        // the even CTA armed but the odd one never loaded have their missing
+        // bytes cancelled, stages only the odd CTA loaded are armed for its bytes.
+        const uint32_t mine = issued, peer = s_peer_issued;
+        const uint32_t lo = mine < peer ? mine : peer, hi = mine < peer ? peer : mine;
+        for (uint32_t i = lo; i < hi; ++i) {
+            uint64_t *fb = &full_bar[i % stages];
+            if (i < mine) sm100::mbar_complete_tx(fb, bytes);
+            else sm100::mbar_arrive_expect_tx(fb, bytes);
+        }
+        const uint32_t first = hi > (uint32_t)stages ? hi - stages : 0;
+        for (uint32_t i = first; i < hi; ++i)
+            sm100::mbar_wait(&full_bar[i % stages], (i / stages) & 1, DRAIN_LIMIT);
+    }
+    sm100::cluster_sync();   // the odd CTA's shared memory outlives its copies
     if (warp == 1) {
         sm100::tc_fence_after();
         sm100::tmem_dealloc_pair(tmem, TMEM_COLS);
@@ -461,8 +479,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
 // ---------------------------------------------------------------- input split
 // One CTA per row: power-of-two scale 2^e >= max|x|, then with s = LEG_SPLIT_FBITS
 //   xs = x 2^-e,  F0 = round(xs 2^s) 2^-s,  r = (xs - F0) 2^s,  F1 = fp16(r),
-// and the five planes  F0, F1, fp16(r - F1), fp16(2^-s F1), 2^-s F0  (plane p
-// at P + p * pstride), so that xs = F0 + 2^-s (F1 + (r - F1)).  Input FP32
+// and the seven planes  F0, F1, fp16(r - F1), fp16(2^-s F1), 2^-s F0,
+// fp16(2^-2s F1), fp16(2^-s (r - F1))  (plane p at P + p * pstride), so that
+// xs = F0 + 2^-s (F1 + (r - F1)).  Input FP32
 // (forward) or a double-float pair (adjoint).  g0 (forward only): row 0 of G,
 // a00 * x[0] as a double-float pair (the operator's row 0 is a00 e_0).
 template <class T> __device__ __forceinline__ float hi_of(T v);
@@ -527,6 +546,8 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
             o[2][i] = __float2half_rn(r - f1f);
             o[3][i] = __float2half_rn(f1f * ISC);
             o[4][i] = __float2half_rn(x0 * ISC);
+            o[5][i] = __float2half_rn(f1f * (ISC * ISC));
+            o[6][i] = __float2half_rn((r - f1f) * ISC);
         }
 #pragma unroll
         for (int p = 0; p < LEG_SPLIT_NF; ++p)
@@ -662,7 +683,7 @@ int max_pairs(int *out)
     if (dev < 0 || dev >= 64) return leg_set_error(LEG_ERR_INVALID_ARG, "device index out of range");
     std::lock_guard<std::mutex> lock(mu);
     if (!cache[dev]) {
-        auto kern = tc_gemm_kernel<6, true>;
+        auto kern = tc_gemm_kernel<8, true>;
         const size_t smem = SMEM_LIMIT - SMEM_STATIC_RESERVE + 1024;
         LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         cudaLaunchConfig_t cfg = {};
@@ -690,7 +711,8 @@ int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int nt
               long long limit, cudaStream_t st)
 {
     if (ntiles <= 0) return LEG_OK;
-    if (tn < 16 || tn > MAX_TN || tn % 16) return leg_set_error(LEG_ERR_INVALID_ARG, "tile width out of range");
+    if (tn < 16 || tn > max_tn<NPROD>() || tn % 16)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "tile width out of range");
     auto kern = tc_gemm_kernel<NPROD, OUT_DF>;
     const int stages = stages_for<NPROD>(tn);
     const size_t smem = (size_t)stages * stage_bytes<NPROD>(tn) + 1024;
@@ -718,36 +740,34 @@ int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int nt
 // Cycles of one pair MMA (M = 256, N = tn, K = 16) on each SM of the pair:
 // the slowest of the tensor rate (128 x tn x 16 MACs at 4096 per cycle), the
 // operand reads from shared memory (4 KB of A plus tn/2 rows of B at 128
-// bytes per cycle) and the issue cost of one pair instruction (about 80
-// cycles, measured on GB300 for tn = 32..128 with CUDA-event and clock64
-// timings of this kernel).
+// bytes per cycle) and the issue cost of one pair instruction from the MMA
+// warp (about 48 cycles, measured on GB300 with clock64 around the issue loop
+// of this kernel for tn = 128..224).
 int mma_cycles(int tn)
 {
     int c = tn / 2;
     if (32 + tn / 8 > c) c = 32 + tn / 8;
-    if (80 > c) c = 80;
+    if (48 > c) c = 48;
     return c;
 }
 
 int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 // Estimated cycles of the busiest pair for ntm row tiles x B functions with
-// K-depth nkb: waves x (per-tile fixed cost + nkb x (12 MMAs + the acc1
-// promotion stall when acc1 has a single TMEM buffer)).
+// K-depth nkb: waves x (per-tile fixed cost + nkb x 16 MMAs).
 long long tile_cost(int tn, int ntm, int B, int nkb, int pairs)
 {
     const long long tiles = (long long)ntm * ceil_div(B, tn);
     const long long waves = (tiles + pairs - 1) / pairs;
-    const long long promo = acc1_buffers(tn) == 1 ? (400 + 3 * tn) / CHUNK_KB : 0;
-    return waves * (2000 + (long long)nkb * (12 * mma_cycles(tn) + promo));
+    return waves * (2000 + (long long)nkb * 16 * mma_cycles(tn));
 }
 
-// Functions per pair tile: the lowest tile_cost, ties to the wider tile.
-int choose_tn(int ntm, int B, int nkb, int pairs)
+// Functions per pair tile (<= maxtn): the lowest tile_cost, ties to the wider tile.
+int choose_tn(int ntm, int B, int nkb, int pairs, int maxtn = 128)
 {
-    int best = MAX_TN;
+    int best = maxtn;
     long long best_cost = -1;
-    for (int tn = MAX_TN; tn >= 16; tn -= 16) {
+    for (int tn = maxtn; tn >= 16; tn -= 16) {
         const long long cost = tile_cost(tn, ntm, B, nkb, pairs);
         if (best_cost < 0 || cost < best_cost) {
             best_cost = cost;
@@ -807,7 +827,7 @@ int leg_split_choose_tn(const leg_plan *p, int B)
 {
     if (p->tn) return p->tn;
     int pairs = 0;
-    if (max_pairs(&pairs)) return MAX_TN;
+    if (max_pairs(&pairs)) return max_tn<8>();
     return choose_tn(ceil_div(p->rows - 1, PAIR_M), B, p->Kp / TILE_K, pairs);
 }
 
@@ -851,7 +871,7 @@ int leg_gemm_split_fwd_into(leg_plan *p, int B, const LegSplitIn &in, float2 *G,
     TcProblem pr;
     int rc = leg_make_split_problem(&pr, p, in, B, G, ldg, leg_split_choose_tn(p, B));
     if (rc) return rc;
-    return launch_tc<6, true>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
+    return launch_tc<8, true>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
 }
 
 int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st)
@@ -874,7 +894,7 @@ int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
     rc = make_split(&pr, p->AhT[0], (size_t)p->K * npr, p->K, npr, p->colexp, in, B, npr, df, p->K,
                     p->tn ? p->tn : choose_tn(ceil_div(p->K, PAIR_M), B, npr / TILE_K, pairs));
     if (rc) return rc;
-    return launch_tc<6, false>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
+    return launch_tc<8, false>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
 }
 
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
@@ -889,7 +909,7 @@ int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st)
     int pairs = 0;
     int rc = max_pairs(&pairs);
     if (rc) return rc;
-    const int tn = p->tn ? p->tn : choose_tn(ceil_div(p->rows, PAIR_M), B, p->Kp / TILE_K, pairs);
+    const int tn = p->tn ? p->tn : choose_tn(ceil_div(p->rows, PAIR_M), B, p->Kp / TILE_K, pairs, max_tn<1>());
     TcProblem pr;
     memset(&pr, 0, sizeof(pr));
     if ((rc = make_map(&pr.a, p->Abf, p->Kp, p->rows, p->Kp, 1, (size_t)p->rows * p->Kp, true, CTA_M))) return rc;
@@ -906,7 +926,7 @@ int leg_gemm_split_grouped(const TcProblem *d_probs, int nprob, int ntiles, int 
 {
     TcProblem dummy;
     memset(&dummy, 0, sizeof(dummy));
-    return launch_tc<6, true>(dummy, d_probs, nprob, ntiles, tn, status, limit, st);
+    return launch_tc<8, true>(dummy, d_probs, nprob, ntiles, tn, status, limit, st);
 }
 
 int leg_split_ragged(const float *f_packed, const long long *in_off, const int *bucket, const int *row,

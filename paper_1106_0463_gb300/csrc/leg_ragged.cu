@@ -195,7 +195,7 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         std::vector<int> cands;
         std::vector<double> cost;
         double best = -1.0;
-        for (int w = 256; w >= 16; w -= 16) {
+        for (int w = 128; w >= 16; w -= 16) {
             double cycles = 0.0, longest = 0.0;
             for (int p = 0; p < nplans; ++p) {
                 if (!r->Bp[p]) continue;
