@@ -193,7 +193,6 @@ ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
 # (profiles/*.md name the captures); keyed by (stage, path, workload).
 TRAFFIC = {
-    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 57383424,   # tc_gemm_pair_split_fp16_...
     ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34175488,         # dct16_forward_dfl_...
 }
 

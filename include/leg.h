@@ -251,6 +251,24 @@ LEG_API int leg_plan_set_tile(leg_plan_t plan, int tn);
 LEG_API int leg_plan_tile_info(leg_plan_t plan, int B, int *tn, int *pairs, int *tiles);
 
 /*
+ * leg_plan_autotune -- choose, by timing on the caller's batch, the launch
+ * parameters that do not change results, and store them in the plan:
+ * the tile width of the tensor-core GEMM (LEG_SPLIT_FP16, LEG_BF16: the
+ * library's model choice and the multiples of 16 from the plan's maximum down
+ * to 64) and the kernel of the FP64 / double-float transform (register-tiled
+ * or shared-memory Stockham).  Not a step of the paper's method: a tuning aid.
+ *   f  device, B x K input (as leg_forward);  c  device, B x N output buffer
+ *      (overwritten).  Synchronises the stream; runs each candidate four times.
+ *   *tn, *fft (either may be NULL): the chosen tile width (0 = the model's
+ *      choice per call) and transform kernel (0 register-tiled, 1 Stockham).
+ * With the environment variable LEG_TUNE_CACHE naming a file, choices are
+ * appended there keyed by (device name, dtype, N, M, K, Q, B) and reused
+ * without timing by later calls with the same key.
+ */
+LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream, int *tn,
+                              int *fft);
+
+/*
  * leg_forward_noalloc -- leg_forward for a LEG_SPLIT_FP16 plan that allocates
  * no device memory.  (The paper has no counterpart: this is a library
  * convenience.)  It is meant for callers that must not allocate at call time,

@@ -73,6 +73,7 @@ def _load():
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
+        "leg_plan_autotune": ([vp, vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_tile_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_ragged_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i, i, vp, vp, vp, vp], i),
         "leg_forward_ragged": ([vp, vp, vp, vp], i),
@@ -184,6 +185,18 @@ class Plan:
     def set_tile(self, tn: int):
         """Functions per CTA-pair tile of the tensor-core GEMM (0 = automatic)."""
         _check(_lib.leg_plan_set_tile(self._h, int(tn)))
+
+    def autotune(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> dict:
+        """leg_plan_autotune: time the GEMM tile widths and the transform
+        kernels on this batch and keep the fastest (synchronises)."""
+        B = f.shape[0] if f.dim() == 2 else -1
+        pf = _dev_tensor(f, self.io_dtype, (B, self.K), "f")
+        if c is None:
+            c = torch.empty((B, self.N), dtype=self.io_dtype, device=f.device)
+        pc = _dev_tensor(c, self.io_dtype, (B, self.N), "c")
+        tn, fft = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.leg_plan_autotune(self._h, pf, pc, B, _stream(stream), ctypes.byref(tn), ctypes.byref(fft)))
+        return {"tn": tn.value, "fft": fft.value}
 
     def tile_info(self, B: int) -> dict:
         """Tile of the split forward GEMM for B functions: tn, resident pairs, tiles."""

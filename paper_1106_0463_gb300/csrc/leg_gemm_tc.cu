@@ -408,9 +408,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
             }
             __syncwarp();
             sm100::tc_fence_after();
-            const int j = j0 + (int)rank * CTA_M + q * 32 + lane;
-            const bool row_ok = j < pr.rows;
-            const int ej = (row_ok && pr.aexp) ? pr.aexp[j] : 0;
+            // acc0 (and acc2, folded into r1) into registers, then release TMEM
+            // before the stores: the MMA warp starts the next tile meanwhile
+            float a0[16 * MU];
 #pragma unroll
             for (int m = 0; m < MU; ++m) {
                 if (cg + 4 * m >= nunits) continue;
@@ -426,6 +426,19 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                 } else {
                     sm100::tmem_ld_wait();
                 }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) a0[16 * m + i] = tv[i];
+            }
+            sm100::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) sm100::mbar_arrive_cluster(acc_empty0);
+
+            const int j = j0 + (int)rank * CTA_M + q * 32 + lane;
+            const bool row_ok = j < pr.rows;
+            const int ej = (row_ok && pr.aexp) ? pr.aexp[j] : 0;
+#pragma unroll
+            for (int m = 0; m < MU; ++m) {
+                if (cg + 4 * m >= nunits) continue;
                 const int bb = b0 + (cg + 4 * m) * 16;
 #pragma unroll
                 for (int i = 0; i < 16; ++i) {
@@ -434,19 +447,15 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     if (!row_ok || bi >= pr.B) continue;
                     const size_t o = (size_t)bi * pr.ldo + j;
                     if constexpr (NPROD == 1) {
-                        static_cast<float *>(pr.out)[o] = tv[i];
+                        static_cast<float *>(pr.out)[o] = a0[16 * m + i];
                     } else if constexpr (OUT_DF) {
-                        const dfl sm = df_two_sum(tv[i], r1[16 * m + i] * W1);
+                        const dfl sm = df_two_sum(a0[16 * m + i], r1[16 * m + i] * W1);
                         static_cast<float2 *>(pr.out)[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
                     } else {
-                        static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], W1, tv[i]), e);
+                        static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], W1, a0[16 * m + i]), e);
                     }
                 }
             }
-            // acc0 / acc2 read: the MMA warp may start the next tile
-            sm100::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) sm100::mbar_arrive_cluster(acc_empty0);
         }
         if (!ok && lane == 0) fail();
     }

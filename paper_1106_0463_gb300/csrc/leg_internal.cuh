@@ -88,6 +88,7 @@ struct leg_plan {
     int *rowexp = nullptr;                        // per-row power-of-two scale (split)
     double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
     int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
+    int fft_variant = 0;      // 0: register-tiled transform (M >= 256), 1: shared-memory Stockham
     // transposed split planes for the adjoint GEMM: K x Kpr (Kpr = rows padded),
     // each column k of the operator scaled by its own power of two
     __half *AhT[3] = {nullptr, nullptr, nullptr};   // one allocation (AhT[s] = AhT[0] + s K Kpr)
