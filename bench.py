@@ -29,6 +29,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -73,7 +74,9 @@ class ClockSampler:
     def __init__(self, gpu_index: str):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%s.csv" % gpu_index)
+        # LEG_CLOCKS_DIR keeps the raw samples; otherwise they go to the temp directory
+        out = os.environ.get("LEG_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, "clocks_bench_%s_%d.csv" % (gpu_index, os.getpid()))
 
     def start(self):
         try:
@@ -191,9 +194,10 @@ DTYPE_STR = {
 ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
-# (profiles/*.md name the captures); keyed by (stage, path, workload).
+# (one ncu capture per kernel); keyed by (stage, path, workload).
 TRAFFIC = {
-    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34175488,         # dct16_forward_dfl_...
+    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 75850752,   # tc_gemm_pair_split_fp16_...
+    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34175744,         # dct16_forward_dfl_...
 }
 
 
@@ -306,6 +310,24 @@ def extra_workloads(leg, torch, flush, rank):
     return out
 
 
+def max_over_ranks(torch, dist, x: float, device) -> float:
+    """The largest value of the host float x over the ranks of the default
+    process group (x itself without one): the whole job lasts as long as its
+    slowest rank."""
+    if dist is None:
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: int, ms_per_step: float) -> float:
+    """Units per second of the whole job: every rank processes its own
+    units_per_rank per step (weak scaling, no exchange between ranks), and the
+    step lasts ms_per_step (the maximum over ranks)."""
+    return world * units_per_rank / (ms_per_step / 1e3)
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import paper_1106_0463_gb300 as leg
@@ -339,12 +361,9 @@ def gpu_arm(args, rank, world, local_rank):
     stage = np.array(res["stage"])              # steps x 3 (ms)
     step_ms = stage.sum(1)
     total_ms = float(step_ms.sum())
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(torch, dist, total_ms, "cuda")
     ms_per_step = total_ms / args.steps
-    value = world * B * N / (ms_per_step / 1e3)
+    value = whole_job_rate(world, B * N, ms_per_step)
     prep_ms, gemm_ms, fft_ms = (float(v) for v in stage.mean(0))
 
     # ---------------- e2e through the public API with pinned host buffers
@@ -364,12 +383,8 @@ def gpu_arm(args, rank, world, local_rank):
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
-    e2e_step = statistics.mean(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_step = float(t.item())
-    e2e = {"value": world * B * N / (e2e_step / 1e3), "unit": UNIT,
+    e2e_step = max_over_ranks(torch, dist, statistics.mean(e2e_ms), "cuda")
+    e2e = {"value": whole_job_rate(world, B * N, e2e_step), "unit": UNIT,
            "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
            "d2h_bytes_per_step": c_host.numel() * c_host.element_size()}
 
@@ -411,7 +426,7 @@ def gpu_arm(args, rank, world, local_rank):
                     "achieved": ops / (fft_ms / 1e3) / 1e12, "peak": peak_alu, "unit": "Tops/s",
                     "ops_per_launch": ops, "hbm_gbs": fft_hbm, "hbm_frac": fft_hbm / hbm,
                     "traffic": TRAFFIC.get(("fft", args.path, name)),
-                    "peak_source": "derived: SMs x lanes x max SM clock (see DESIGN.md)"}
+                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"}
         fft_roof["frac"] = fft_roof["achieved"] / peak_alu
     else:
         fft_roof = {"kernel": "fft_forward_kernel (FFT stage)", "bound": "hbm", "achieved": fft_hbm, "peak": hbm,

@@ -34,28 +34,30 @@
 //
 // Kernel: persistent, CTA pairs (cluster of 2, tcgen05 cta_group::2).  A pair
 // tile is 256 operator rows (MMA M; 128 per CTA = its TMEM lanes) by tn
-// functions (MMA N, 16 <= tn <= 256; each CTA stages tn/2 of them), and
-// K advances in blocks of 32 (one 64-byte swizzle row of FP16).
+// functions (MMA N, a multiple of 16 up to 128 for the split path and 256 for
+// BF16; each CTA stages tn/2 of them), and K advances in blocks of 32 (one
+// 64-byte swizzle row of FP16).
 //   warp 0         TMA producer (each CTA): its operator tiles (128 rows) and
-//                  input tiles (tn/2 rows) of a K block into one of the stages,
-//                  armed on its own full barrier;
-//   warp 1         even CTA: issues the pair MMAs (M=256, N=tn, K=16) once both
-//                  CTAs' copies of a stage landed, commits each stage back to
-//                  both producers and each finished chunk to both epilogues;
-//                  odd CTA: relays its full barriers to the even CTA;
+//                  input tiles (tn/2 rows) of a K block into one of the stages;
+//                  the copies of both CTAs complete on the even CTA's full
+//                  barrier (cta_group::2 TMA);
+//   warp 1         even CTA: issues the pair MMAs (M=256, N=tn, K=16) once a
+//                  stage is full, commits each stage back to both producers
+//                  and each finished chunk / tile to both epilogues (multicast
+//                  commits); odd CTA: idle after the TMEM allocation;
 //                  (the producer and MMA loops run on the whole warp, so that
 //                  descriptors and coordinates stay warp-uniform; one elected
 //                  lane issues the TMA, MMA and commit instructions)
 //   warps 2..17    epilogue (each CTA, own TMEM lanes): chunk promotion into
 //                  registers, then scaling and double-float stores.
-// TMEM: acc0 in columns [0, tn); acc1 in two chunk buffers [tn, 2tn) and
-// [2tn, 3tn) when tn <= 160 (the MMAs of one chunk overlap the promotion of
-// the previous one), else in one buffer [256, 256 + tn) (the MMAs pause while
-// a chunk is promoted).  Each pair MMA costs about 80 cycles to issue, so wide
-// tiles (tn up to 256, N/2 cycles of tensor work per MMA) keep the tensor
-// pipe busy.  Every wait is bounded by a cycle limit; on expiry the kernel
-// records LEG_ERR_TIMEOUT in the status word, tells the other CTA of the pair,
-// drains its own TMA copies and MMAs (again bounded), releases TMEM and returns.
+// TMEM (split path): acc0 in columns [0, tn), acc2 in [tn, 2tn), acc1 chunk
+// buffer b in [(2 + b) tn, (3 + b) tn); the MMAs of one chunk overlap the
+// promotion of the previous one.  BF16: one accumulator in [0, tn).  The
+// epilogue copies acc0 and acc2 to registers and releases the tile's TMEM
+// before its global stores, so the next tile's MMAs overlap them.  Every wait
+// is bounded by a cycle limit; on expiry the kernel records LEG_ERR_TIMEOUT in
+// the status word, tells the other CTA of the pair, drains its own TMA copies
+// and MMAs (again bounded), releases TMEM and returns.
 #include <stdio.h>
 #include <string.h>
 
