@@ -220,12 +220,12 @@ def relerr(c, ref):
     return float(np.max(np.max(np.abs(c - ref), 1) / np.max(np.abs(ref), 1)))
 
 
-def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0):
+def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, flags=0):
     cfg = workloads.CONFIGS[name]
     B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
     dt = PATHS[path]
     t0 = time.time()
-    plan = leg.Plan(N, M, K, 0, dt)
+    plan = leg.Plan(N, M, K, 0, dt, flags=flags)
     torch.cuda.synchronize()
     plan_s = time.time() - t0
     f_np = workloads.workload_inputs(name, salt=rank)
@@ -461,6 +461,21 @@ def gpu_arm(args, rank, world, local_rank):
             extras[p_name + "_gpu_path"] = {"value": B * N / (ms / 1e3), "ms_per_step": ms,
                                             "max_rel_err": relerr(r["c_sample"], ref)}
             del r
+    if not args.no_extras and args.path == "split_fp16":
+        # the same map with L = R A multiplied out at plan time: split + one GEMM
+        r = run_path(leg, torch, name, "split_fp16", rank, 10, 3, flush, sample_err=16, flags=leg.FLAG_COLLAPSED)
+        st_ms = np.array(r["stage"]).mean(0)
+        ms = float(np.array(r["stage"]).sum(1).mean())
+        cf_useful = 2.0 * B * N * K
+        cf_exec = 8 * 2.0 * B * N * Kp
+        extras["collapsed_split_fp16"] = {
+            "value": B * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "max_rel_err": relerr(r["c_sample"], ref),
+            "input_split_ms": float(st_ms[0]), "gemm_ms": float(st_ms[1]), "plan_build_s": r["plan_s"],
+            "gemm_useful_tflops": cf_useful / (st_ms[1] / 1e3) / 1e12,
+            "gemm_executed_tflops": cf_exec / (st_ms[1] / 1e3) / 1e12,
+            "gemm_executed_frac": cf_exec / (st_ms[1] / 1e3) / 1e12 / peak_tensor,
+            "launches_per_step": 2}
+        del r
     if not args.no_extras:
         extras.update(extra_workloads(leg, torch, flush, rank))
     cpu = None

@@ -62,12 +62,12 @@ extern "C" {
  *   LEG_F32        f, c in FP32; FP32 GEMM on the CUDA cores (FFMA), FP32 FFT.
  *   LEG_BF16       f, c in FP32; one BF16 x BF16 tensor-core product with
  *                  FP32 accumulation (tcgen05), FP32 FFT.
- *   LEG_SPLIT_FP16 f, c in FP32; operator and input each split into three
- *                  FP16 slices (a fixed-point leading slice, two residual
- *                  slices), eight tcgen05 products into four FP32 TMEM
- *                  accumulators of which the leading one is exact, combined
- *                  into a double-float result; double-float FFT.  The path
- *                  aimed at a 1e-6 relative error.
+ *   LEG_SPLIT_FP16 f, c in FP32; operator split into three FP16 slices (a
+ *                  fixed-point leading slice, two residual slices), input
+ *                  into seven pre-scaled FP16 planes; eight tcgen05 products
+ *                  into three FP32 TMEM accumulators of which the leading one
+ *                  is exact, combined into a double-float result;
+ *                  double-float FFT.  The path aimed at a 1e-6 relative error.
  */
 typedef enum {
     LEG_F64 = 0,
@@ -80,6 +80,21 @@ typedef enum {
 #define LEG_FLAG_TAU_LITERAL 1u  /* Q-point Gauss rule mapped onto tau in [0,1]
                                     instead of the nonnegative half of a
                                     2Q-point rule (the default)               */
+/*
+ * LEG_FLAG_COLLAPSED: the plan multiplies out, at plan time and in FP64, the
+ * whole linear map of Theorem 1 (Eq. 2.4, Eq. 2.5) on sampled inputs,
+ *     L = R A   (N x K),  c = L f,
+ * A the (M/2+1) x K Abel-interpolation operator and R the N x (M/2+1)
+ * matrix of the twisted transform with the (2n+1) factor (computed by
+ * applying the plan's FP64 transform to the columns of A).  leg_forward is
+ * then one GEMM with no transform stage and leg_backward one transposed
+ * GEMM (df = L^T dc), in the plan's dtype.  The paper evaluates the map as
+ * the Abel step followed by an FFT; the collapsed form is the same linear
+ * map (up to rounding) with a different factorisation, cheaper when N < M/2
+ * and the batch is large.  Ragged batches and leg_forward_noalloc take plans
+ * without this flag.
+ */
+#define LEG_FLAG_COLLAPSED   2u
 
 typedef struct leg_plan *leg_plan_t;
 

@@ -21,13 +21,14 @@ import re
 import torch
 
 __all__ = [
-    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB",
+    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FLAG_COLLAPSED", "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB",
     "Ragged", "sample_cl",
     "LegError", "Plan", "LegendreFn", "legendre", "library_path", "declared_symbols", "load_library",
 ]
 
 F64, F32, BF16, SPLIT_FP16 = 0, 1, 2, 3
 FLAG_TAU_LITERAL = 1
+FLAG_COLLAPSED = 2    # c = L f with L = R A multiplied out at plan time (one GEMM, no transform)
 FAMILY_GENFN, FAMILY_EXP, FAMILY_CHEB = 0, 1, 2
 _ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 

@@ -33,6 +33,7 @@ void free_plan(leg_plan *p)
     cudaFree(p->omt2);
     cudaFree(p->wq);
     cudaFree(p->A64);
+    cudaFree(p->L64);
     cudaFree(p->A32);
     cudaFree(p->Ah[0]);    // the three planes share one allocation
     cudaFree(p->AhT[0]);
@@ -62,10 +63,14 @@ int ensure_workspace(leg_plan *p, int B)
     const size_t eb = g_elem_bytes(p->dtype);
     const size_t Bz = (size_t)B;
     const int rowsKp = leg_round_up(p->rows, 8);
-    const int bwdKp = (p->dtype == LEG_SPLIT_FP16) ? leg_round_up(rowsKp, LEG_KPAD) : 0;
-    p->ldg = (p->dtype == LEG_SPLIT_FP16) ? bwdKp : rowsKp;
-    LEG_CUDA_TRY(cudaMalloc(&p->G, eb * Bz * p->ldg));
-    LEG_CUDA_TRY(cudaMalloc(&p->Gbar, eb * Bz * p->ldg));
+    const int bwdKp = (p->dtype == LEG_SPLIT_FP16) ? leg_adj_depth(p) : 0;
+    if (p->collapsed()) {
+        p->ldg = 0;   // one GEMM straight into c / df: no G
+    } else {
+        p->ldg = (p->dtype == LEG_SPLIT_FP16) ? bwdKp : rowsKp;
+        LEG_CUDA_TRY(cudaMalloc(&p->G, eb * Bz * p->ldg));
+        LEG_CUDA_TRY(cudaMalloc(&p->Gbar, eb * Bz * p->ldg));
+    }
     if (p->dtype == LEG_SPLIT_FP16) {
         // input planes serve both directions: B x Kp (forward) or B x bwdKp (adjoint)
         p->ldf = (p->Kp > bwdKp) ? p->Kp : bwdKp;
@@ -111,7 +116,7 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
         return leg_set_error(LEG_ERR_INVALID_ARG, "Q must be in [0, 16384]");
     if (dtype < LEG_F64 || dtype > LEG_SPLIT_FP16)
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown dtype");
-    if (flags & ~LEG_FLAG_TAU_LITERAL)
+    if (flags & ~(LEG_FLAG_TAU_LITERAL | LEG_FLAG_COLLAPSED))
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown flag");
 
     leg_plan *p = new (std::nothrow) leg_plan();
@@ -237,6 +242,37 @@ int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, c
     if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
     if ((rc = ensure_workspace(p, B))) return rc;
     if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[0], st));
+    if (p->collapsed()) {
+        // c = L f: one GEMM into c, no transform stage
+        switch (p->dtype) {
+        case LEG_F64:
+            if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+            rc = leg_gemm_f64_fwd(static_cast<const double *>(f), p->K, p->L64, p->K, static_cast<double *>(c),
+                                  p->N, B, p->N, p->K, st);
+            break;
+        case LEG_F32:
+            if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+            rc = leg_gemm_f32_fwd(static_cast<const float *>(f), p->K, p->A32, p->K, static_cast<float *>(c), p->N,
+                                  B, p->N, p->K, st);
+            break;
+        case LEG_SPLIT_FP16:
+            rc = leg_split_prepare_input(p, static_cast<const float *>(f), B, st);
+            if (!rc && ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+            if (!rc) rc = leg_gemm_split_collapsed_fwd(p, B, static_cast<float *>(c), st);
+            break;
+        case LEG_BF16:
+            rc = leg_bf16_prepare_input(p, static_cast<const float *>(f), B, st);
+            if (!rc && ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
+            if (!rc) rc = leg_gemm_bf16_fwd(p, B, c, p->N, st);
+            break;
+        }
+        if (rc) return rc;
+        if (ev) {
+            LEG_CUDA_TRY(cudaEventRecord(ev[2], st));
+            LEG_CUDA_TRY(cudaEventRecord(ev[3], st));
+        }
+        return LEG_OK;
+    }
     switch (p->dtype) {
     case LEG_F64:
         if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
@@ -256,7 +292,7 @@ int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, c
     case LEG_BF16:
         rc = leg_bf16_prepare_input(p, static_cast<const float *>(f), B, st);
         if (!rc && ev) LEG_CUDA_TRY(cudaEventRecord(ev[1], st));
-        if (!rc) rc = leg_gemm_bf16_fwd(p, B, st);
+        if (!rc) rc = leg_gemm_bf16_fwd(p, B, p->G, p->ldg, st);
         break;
     }
     if (rc) return rc;
@@ -298,6 +334,21 @@ extern "C" int leg_backward(leg_plan_t p, const void *dc, void *df, int B, cudaS
     if (B == 0) return LEG_OK;
     if (!dc || !df) return leg_set_error(LEG_ERR_INVALID_ARG, "null dc or df");
     if ((rc = ensure_workspace(p, B))) return rc;
+    if (p->collapsed()) {
+        // df = L^T dc: one transposed GEMM
+        switch (p->dtype) {
+        case LEG_F64:
+            return leg_gemm_f64_adj(static_cast<const double *>(dc), p->N, p->L64, p->K, static_cast<double *>(df),
+                                    p->K, B, p->N, p->K, st);
+        case LEG_F32:
+            return leg_gemm_f32_adj(static_cast<const float *>(dc), p->N, p->A32, p->K, static_cast<float *>(df),
+                                    p->K, B, p->N, p->K, st);
+        case LEG_SPLIT_FP16:
+            return leg_gemm_split_collapsed_adj(p, static_cast<const float *>(dc), df, B, st);
+        default:
+            return leg_set_error(LEG_ERR_UNSUPPORTED, "leg_backward is not available for LEG_BF16");
+        }
+    }
     if ((rc = leg_fft_adjoint(p, dc, p->Gbar, p->ldg, B, st))) return rc;
     switch (p->dtype) {
     case LEG_F64:
@@ -328,7 +379,7 @@ extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params,
     // B x ldg x 4 bytes, so use the backward buffer pair as one FP64 array when needed
     double *G = nullptr;
     int ldg = leg_round_up(p->rows, 8);
-    if (g_elem_bytes(p->dtype) >= sizeof(double)) {
+    if (g_elem_bytes(p->dtype) >= sizeof(double) && p->G) {
         G = static_cast<double *>(p->G);
         ldg = p->ldg;
     } else {
@@ -382,6 +433,6 @@ extern "C" int leg_plan_tile_info(leg_plan_t p, int B, int *tn, int *pairs, int 
     const int t = leg_split_choose_tn(p, B);
     if (tn) *tn = t;
     if (pairs) *pairs = np;
-    if (tiles) *tiles = ((p->rows - 1 + 255) / 256) * ((B + t - 1) / t);
+    if (tiles) *tiles = ((leg_split_fwd_rows(p) + 255) / 256) * ((B + t - 1) / t);
     return LEG_OK;
 }

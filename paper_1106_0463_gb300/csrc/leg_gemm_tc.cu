@@ -839,18 +839,21 @@ int leg_split_choose_tn(const leg_plan *p, int B)
     if (p->tn) return p->tn;
     int pairs = 0;
     if (max_pairs(&pairs)) return max_tn<8>();
-    return choose_tn(ceil_div(p->rows - 1, PAIR_M), B, p->Kp / TILE_K, pairs);
+    return choose_tn(ceil_div(leg_split_fwd_rows(p), PAIR_M), B, p->Kp / TILE_K, pairs);
 }
+
+int leg_split_fwd_rows(const leg_plan *p) { return p->collapsed() ? p->N : p->rows - 1; }
 
 int leg_build_split_transposed(leg_plan *p)
 {
-    const int npr = leg_round_up(leg_round_up(p->rows, 8), LEG_KPAD);
+    const int npr = leg_adj_depth(p);
     const size_t plane = (size_t)p->K * npr;
     LEG_CUDA_TRY(cudaMalloc(&p->AhT[0], sizeof(__half) * 3 * plane));
     p->AhT[1] = p->AhT[0] + plane;
     p->AhT[2] = p->AhT[0] + 2 * plane;
     LEG_CUDA_TRY(cudaMalloc(&p->colexp, sizeof(int) * p->K));
-    split_cols_kernel<<<p->K, 256>>>(p->A64, p->rows, p->K, npr, p->AhT[0], p->AhT[1], p->AhT[2], p->colexp);
+    split_cols_kernel<<<p->K, 256>>>(p->collapsed() ? p->L64 : p->A64, p->grows, p->K, npr, p->AhT[0], p->AhT[1],
+                                     p->AhT[2], p->colexp);
     LEG_LAUNCH_CHECK("split_cols_kernel");
     return LEG_OK;
 }
@@ -865,7 +868,9 @@ int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const
 
 int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
 {
-    return leg_split_prepare_input_into(p, f, B, leg_split_workspace(p), static_cast<float2 *>(p->G), p->ldg, st);
+    // collapsed plans have no G (row 0 of G is written by the split otherwise)
+    return leg_split_prepare_input_into(p, f, B, leg_split_workspace(p),
+                                        p->collapsed() ? nullptr : static_cast<float2 *>(p->G), p->ldg, st);
 }
 
 // Forward split problem: operator rows 1..rows-1 (row 0 is a00 e_0 and is
@@ -890,14 +895,11 @@ int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st)
     return leg_gemm_split_fwd_into(p, B, leg_split_workspace(p), static_cast<float2 *>(p->G), p->ldg, st);
 }
 
-int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
+// df[b, k] = sum_j in[b, j] S[j, k] from the split planes `in` (B x npr) of
+// the cotangent and the transposed planes of the plan's operator S.
+int split_adj_gemm(leg_plan *p, const LegSplitIn &in, void *df, int B, cudaStream_t st)
 {
-    // Gbar (double-float, B x ldg, rows valid) -> split planes B x npr
-    const int npr = leg_round_up(leg_round_up(p->rows, 8), LEG_KPAD);
-    const LegSplitIn in = leg_split_workspace(p);
-    split_rows_kernel<float2><<<B, SPLIT_THREADS, 0, st>>>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows, npr, in,
-                                                 nullptr, 0, 0.0);
-    LEG_LAUNCH_CHECK("split_rows_kernel (adjoint)");
+    const int npr = leg_adj_depth(p);
     int pairs = 0;
     int rc = max_pairs(&pairs);
     if (rc) return rc;
@@ -908,6 +910,36 @@ int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
     return launch_tc<8, false>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
 }
 
+int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
+{
+    // Gbar (double-float, B x ldg, rows valid) -> split planes B x npr
+    const LegSplitIn in = leg_split_workspace(p);
+    split_rows_kernel<float2><<<B, SPLIT_THREADS, 0, st>>>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows,
+                                                           leg_adj_depth(p), in, nullptr, 0, 0.0);
+    LEG_LAUNCH_CHECK("split_rows_kernel (adjoint)");
+    return split_adj_gemm(p, in, df, B, st);
+}
+
+// Collapsed plans: c = L f in one split GEMM (L's rows on the MMA's M side),
+// FP32 output; no transform stage.
+int leg_gemm_split_collapsed_fwd(leg_plan *p, int B, float *c, cudaStream_t st)
+{
+    TcProblem pr;
+    int rc = make_split(&pr, p->Ah[0], (size_t)p->N * p->Kp, p->N, p->Kp, p->rowexp, leg_split_workspace(p), B,
+                        p->Kp, c, p->N, leg_split_choose_tn(p, B));
+    if (rc) return rc;
+    return launch_tc<8, false>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
+}
+
+// Collapsed plans: df = L^T dc (dc FP32, B x N).
+int leg_gemm_split_collapsed_adj(leg_plan *p, const float *dc, void *df, int B, cudaStream_t st)
+{
+    const LegSplitIn in = leg_split_workspace(p);
+    split_rows_kernel<float><<<B, SPLIT_THREADS, 0, st>>>(dc, p->N, p->N, leg_adj_depth(p), in, nullptr, 0, 0.0);
+    LEG_LAUNCH_CHECK("split_rows_kernel (collapsed adjoint)");
+    return split_adj_gemm(p, in, df, B, st);
+}
+
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
 {
     bf16_rows_kernel<<<B, 256, 0, st>>>(f, p->K, p->Kp, p->Fbf);
@@ -915,17 +947,18 @@ int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_
     return LEG_OK;
 }
 
-int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st)
+int leg_gemm_bf16_fwd(leg_plan *p, int B, void *out, int ldo, cudaStream_t st)
 {
     int pairs = 0;
     int rc = max_pairs(&pairs);
     if (rc) return rc;
-    const int tn = p->tn ? p->tn : choose_tn(ceil_div(p->rows, PAIR_M), B, p->Kp / TILE_K, pairs, max_tn<1>());
+    const int rows = p->grows;
+    const int tn = p->tn ? p->tn : choose_tn(ceil_div(rows, PAIR_M), B, p->Kp / TILE_K, pairs, max_tn<1>());
     TcProblem pr;
     memset(&pr, 0, sizeof(pr));
-    if ((rc = make_map(&pr.a, p->Abf, p->Kp, p->rows, p->Kp, 1, (size_t)p->rows * p->Kp, true, CTA_M))) return rc;
+    if ((rc = make_map(&pr.a, p->Abf, p->Kp, rows, p->Kp, 1, (size_t)rows * p->Kp, true, CTA_M))) return rc;
     if ((rc = make_map(&pr.f, p->Fbf, p->Kp, B, p->Kp, 1, (size_t)B * p->Kp, true, tn / 2))) return rc;
-    finish_problem(&pr, nullptr, nullptr, p->G, p->ldg, p->rows, B, p->Kp, tn);
+    finish_problem(&pr, nullptr, nullptr, out, ldo, rows, B, p->Kp, tn);
     return launch_tc<1, false>(pr, nullptr, 1, tiles_of(pr), tn, p->status, p->wait_limit, st);
 }
 

@@ -79,6 +79,10 @@ struct leg_plan {
     double *wq = nullptr;
     // operator, FP64, rows x K (ld = K); kept for every dtype (adjoint, checks)
     double *A64 = nullptr;
+    // LEG_FLAG_COLLAPSED: L = R A, FP64, N x K (ld = K); the per-dtype planes
+    // below (A32, Ah, Abf, AhT) then hold L instead of A
+    double *L64 = nullptr;
+    int grows = 0;   // rows of the operator the planes hold: rows (Abel) or N (collapsed)
     // FP32 copy (LEG_F32), rows x K
     float *A32 = nullptr;
     // tensor-core planes, rows x Kp, K-major
@@ -89,6 +93,7 @@ struct leg_plan {
     double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
     int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
     int fft_variant = 0;      // 0: register-tiled transform (M >= 256), 1: shared-memory Stockham
+    bool collapsed() const { return (flags & LEG_FLAG_COLLAPSED) != 0; }
     // transposed split planes for the adjoint GEMM: K x Kpr (Kpr = rows padded),
     // each column k of the operator scaled by its own power of two
     __half *AhT[3] = {nullptr, nullptr, nullptr};   // one allocation (AhT[s] = AhT[0] + s K Kpr)
@@ -155,6 +160,7 @@ struct LegRaggedBucket {
 // operator build (leg_operator.cu)
 int leg_build_operator(leg_plan *p);   // FP64 operator, then leg_build_planes
 int leg_build_planes(leg_plan *p);
+int leg_build_collapsed(leg_plan *p);   // L = R A for LEG_FLAG_COLLAPSED
 int leg_build_twiddles(leg_plan *p);
 
 // SIMT GEMMs (leg_gemm_simt.cu)
@@ -192,10 +198,17 @@ int leg_plain_g(const leg_plan *p, int family, const double *params, int B, doub
 LegSplitIn leg_split_workspace(const leg_plan *p);
 int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st);
-int leg_gemm_bf16_fwd(leg_plan *p, int B, cudaStream_t st);
+int leg_gemm_bf16_fwd(leg_plan *p, int B, void *out, int ldo, cudaStream_t st);   // rows p->grows
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st);
 int leg_build_split_transposed(leg_plan *p);
+// collapsed plans (LEG_FLAG_COLLAPSED): c = L f and df = L^T dc, FP32
+int leg_gemm_split_collapsed_fwd(leg_plan *p, int B, float *c, cudaStream_t st);
+int leg_gemm_split_collapsed_adj(leg_plan *p, const float *dc, void *df, int B, cudaStream_t st);
+// operator rows of the forward split GEMM: M/2 (row 0 goes through the split) or N (collapsed)
+int leg_split_fwd_rows(const leg_plan *p);
+// K-depth of the adjoint split GEMM: the operator's rows padded to LEG_KPAD
+inline int leg_adj_depth(const leg_plan *p) { return leg_round_up(leg_round_up(p->grows, 8), LEG_KPAD); }
 int leg_make_split_problem(TcProblem *pr, const leg_plan *p, const LegSplitIn &in, int B, float2 *G, int ldg,
                            int tn);
 int leg_split_problem_tiles(const TcProblem &pr);

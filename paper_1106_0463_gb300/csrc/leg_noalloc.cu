@@ -64,6 +64,8 @@ extern "C" int leg_forward_noalloc(leg_plan_t p, const float *f, float *c, int B
     if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
     if (p->dtype != LEG_SPLIT_FP16)
         return leg_set_error(LEG_ERR_INVALID_ARG, "leg_forward_noalloc needs a LEG_SPLIT_FP16 plan");
+    if (p->collapsed())
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "leg_forward_noalloc takes plans without LEG_FLAG_COLLAPSED");
     if (B < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0");
     if (B == 0) return LEG_OK;
     if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");

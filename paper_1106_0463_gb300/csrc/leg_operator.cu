@@ -213,6 +213,29 @@ __global__ void plane_split_kernel(const double *A, int K, int Kp, __half *A0p, 
     }
 }
 
+// out[c * ldo + r] = in[r * ldi + c] for r < R, c < C (32 x 32 tiles, 32 x 8 threads).
+__global__ void transpose_f64_kernel(const double *__restrict__ in, int ldi, double *__restrict__ out, int ldo,
+                                     int R, int C)
+{
+    __shared__ double t[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int r = r0 + i, c = c0 + threadIdx.x;
+        if (r < R && c < C) t[i][threadIdx.x] = in[(size_t)r * ldi + c];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int c = c0 + i, r = r0 + threadIdx.x;
+        if (r < R && c < C) out[(size_t)c * ldo + r] = t[threadIdx.x][i];
+    }
+}
+
+void transpose_f64(const double *in, int ldi, double *out, int ldo, int R, int C)
+{
+    dim3 grid((C + 31) / 32, (R + 31) / 32), block(32, 8);
+    transpose_f64_kernel<<<grid, block>>>(in, ldi, out, ldo, R, C);
+}
+
 __global__ void twiddle_kernel(int M, double2 *t64, float2 *t32, float4 *tdf)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,10 +303,56 @@ int leg_build_operator(leg_plan *p)
     return leg_build_planes(p);
 }
 
-// Operand planes of the plan's dtype, derived from the FP64 operator.
+// LEG_FLAG_COLLAPSED: L = R A (N x K, FP64), row n of L giving c_n of Eq. 2.4
+// with the twist of Eq. 2.5 from the K samples.  Column k of L is the plan's
+// FP64 transform (twist, first difference, (2n+1)) of column k of A, so the
+// columns of A are transposed into rows, transformed as a batch of K
+// "functions", and the result transposed back.
+int leg_build_collapsed(leg_plan *p)
+{
+    const int K = p->K, rows = p->rows, N = p->N;
+    const int ldt = leg_round_up(rows, 8);
+    double *AT = nullptr, *LT = nullptr;
+    auto fail = [&](cudaError_t e, const char *what) {
+        cudaFree(AT);
+        cudaFree(LT);
+        return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
+                             std::string(what) + ": " + cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&AT, sizeof(double) * (size_t)K * ldt)) != cudaSuccess) return fail(e, "collapsed operator");
+    if ((e = cudaMalloc(&LT, sizeof(double) * (size_t)K * N)) != cudaSuccess) return fail(e, "collapsed operator");
+    if ((e = cudaMalloc(&p->L64, sizeof(double) * (size_t)N * K)) != cudaSuccess)
+        return fail(e, "collapsed operator");
+    if ((e = cudaMemset(AT, 0, sizeof(double) * (size_t)K * ldt)) != cudaSuccess) return fail(e, "collapsed operator");
+    transpose_f64(p->A64, K, AT, ldt, rows, K);
+    int rc = leg_fft_forward_f64(p, AT, ldt, LT, K, 0);
+    if (rc) {
+        cudaFree(AT);
+        cudaFree(LT);
+        return rc;
+    }
+    transpose_f64(LT, N, p->L64, K, K, N);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "collapsed operator");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "collapsed operator");
+    cudaFree(AT);
+    cudaFree(LT);
+    return LEG_OK;
+}
+
+// Operand planes of the plan's dtype, derived from the FP64 operator (A, or
+// L = R A for collapsed plans).
 int leg_build_planes(leg_plan *p)
 {
-    const int K = p->K, rows = p->rows;
+    const int K = p->K;
+    const bool col = p->collapsed();
+    if (col && !p->L64) {
+        int rc = leg_build_collapsed(p);
+        if (rc) return rc;
+    }
+    const double *S = col ? p->L64 : p->A64;
+    const int rows = col ? p->N : p->rows;
+    p->grows = rows;
     auto cleanup = []() {};
 #define LEG_TRY_CLEAN(expr)                                                         \
     do {                                                                            \
@@ -297,17 +366,17 @@ int leg_build_planes(leg_plan *p)
     if (p->dtype == LEG_F32) {
         size_t n = (size_t)rows * K;
         LEG_TRY_CLEAN(cudaMalloc(&p->A32, sizeof(float) * n));
-        plane_f32_kernel<<<(unsigned)((n + 255) / 256), 256>>>(p->A64, p->A32, n);
+        plane_f32_kernel<<<(unsigned)((n + 255) / 256), 256>>>(S, p->A32, n);
     } else if (p->dtype == LEG_BF16) {
         LEG_TRY_CLEAN(cudaMalloc(&p->Abf, sizeof(__nv_bfloat16) * (size_t)rows * p->Kp));
-        plane_bf16_kernel<<<rows, 256>>>(p->A64, K, p->Kp, p->Abf);
+        plane_bf16_kernel<<<rows, 256>>>(S, K, p->Kp, p->Abf);
     } else if (p->dtype == LEG_SPLIT_FP16) {
         const size_t plane = (size_t)rows * p->Kp;
         LEG_TRY_CLEAN(cudaMalloc(&p->Ah[0], sizeof(__half) * 3 * plane));
         p->Ah[1] = p->Ah[0] + plane;
         p->Ah[2] = p->Ah[0] + 2 * plane;
         LEG_TRY_CLEAN(cudaMalloc(&p->rowexp, sizeof(int) * rows));
-        plane_split_kernel<<<rows, 256>>>(p->A64, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp);
+        plane_split_kernel<<<rows, 256>>>(S, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp);
         LEG_TRY_CLEAN(cudaGetLastError());
         int rc2 = leg_build_split_transposed(p);
         if (rc2) {
@@ -318,7 +387,8 @@ int leg_build_planes(leg_plan *p)
     LEG_TRY_CLEAN(cudaGetLastError());
     LEG_TRY_CLEAN(cudaDeviceSynchronize());
     // row 0 (y = 0: every quadrature point is x = 1, the node k = 0) is a00 e_0
-    if (p->dtype == LEG_SPLIT_FP16) LEG_TRY_CLEAN(cudaMemcpy(&p->a00, p->A64, sizeof(double), cudaMemcpyDeviceToHost));
+    if (p->dtype == LEG_SPLIT_FP16 && !col)
+        LEG_TRY_CLEAN(cudaMemcpy(&p->a00, p->A64, sizeof(double), cudaMemcpyDeviceToHost));
 #undef LEG_TRY_CLEAN
     return LEG_OK;
 }

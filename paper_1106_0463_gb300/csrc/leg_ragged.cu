@@ -143,6 +143,8 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         if (!plans[p]) return leg_set_error(LEG_ERR_INVALID_ARG, "null plan");
         if (plans[p]->dtype != LEG_SPLIT_FP16)
             return leg_set_error(LEG_ERR_UNSUPPORTED, "ragged batches need LEG_SPLIT_FP16 plans");
+        if (plans[p]->collapsed())
+            return leg_set_error(LEG_ERR_UNSUPPORTED, "ragged batches take plans without LEG_FLAG_COLLAPSED");
         if (plans[p]->device != dev) return leg_set_error(LEG_ERR_INVALID_ARG, "plan on another device");
     }
     for (int i = 0; i < count; ++i) {

@@ -120,7 +120,7 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
             }
             p->tn = best_tn;
         }
-        if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) {
+        if ((p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) && !p->collapsed()) {   // collapsed: no transform
             float t0 = 0.0f, t1 = 0.0f;
             p->fft_variant = 0;
             if ((rc = time_stage(p, f, c, B, st, 2, 3, &t0))) return rc;
