@@ -360,6 +360,7 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
         v[b] = {F::norm(yy[0]), F::norm(yy[1])};
     }
     const T_ x1 = F::norm(F::add(F::sub(load(0), load(L)), F::pow2(fn_sum<R, LOG2H>(part, t, wsum), 1)));
+    fsync<T>();   // load() may read buf (the staged row): all reads precede the first pass's writes
 
     // 2. FFT of length H: Stockham passes of radix E (the last one smaller)
     int Ns = 1;
@@ -454,7 +455,23 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_f
     T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * D::SLOTS) + grp * D::WARPS;
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
     const bool live = blockIdx.x * D::FPB + grp < B;
-    const typename Ar<R>::GT *g = G + (size_t)f * ldg;
+    leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
+    using GT = typename Ar<R>::GT;
+    // Stage the group's row of G (L + 1 values, rounded up to 16 bytes; rows
+    // are 16-byte aligned with at least one padding element) in buf, which
+    // the fold reads before the first pass overwrites it: every 16-byte copy
+    // of the row is in flight at once.
+    {
+        constexpr int BYTES = ((D::L + 1) * (int)sizeof(GT) + 15) / 16 * 16;
+        static_assert(BYTES <= D::SLOTS * (int)sizeof(CxT<R>), "row of G exceeds the exchange buffer");
+        const char *src = reinterpret_cast<const char *>(G + (size_t)f * ldg);
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
+        for (int o = 16 * t; o < BYTES; o += 16 * D::T)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o), "l"(src + o) : "memory");
+        asm volatile("cp.async.wait_all;" ::: "memory");
+    }
+    fsync<D::T>();
+    const GT *g = reinterpret_cast<const GT *>(buf);
     dct16<R, LOG2H>(buf, wsum, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
@@ -524,10 +541,21 @@ int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cu
     const size_t smem = d16_smem<R, LOG2H>();
     LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (B + D::FPB - 1) / D::FPB;
-    kern<<<grid, D::THREADS, smem, st>>>(static_cast<const typename Ar<R>::GT *>(G), ldg,
-                                         static_cast<typename Ar<R>::OUT *>(c), N, B,
-                                         static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out);
-    LEG_LAUNCH_CHECK("dct16_forward_kernel");
+    // programmatic dependent launch: CTAs start on SMs the GEMM has left
+    // while its last tiles finish, and wait there for G
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(D::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, static_cast<const typename Ar<R>::GT *>(G), ldg,
+                                    static_cast<typename Ar<R>::OUT *>(c), N, B,
+                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out));
     return LEG_OK;
 }
 

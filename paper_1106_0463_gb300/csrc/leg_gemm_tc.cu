@@ -208,6 +208,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     sm100::cluster_sync();
     sm100::tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    // launched as a dependent of the input split: the setup above overlaps its
+    // tail; the inputs (planes, scales) and the output are touched only below
+    leg_griddep_wait();
+    leg_griddep_trigger();
 
     const uint32_t peer_abort = sm100::mapa_shared(sm100::smem_u32(const_cast<int *>(&s_abort)), rank ^ 1u);
     auto fail = [&]() {
@@ -502,7 +506,8 @@ template <class T> __device__ __forceinline__ float lo_of(T v);
 template <> __device__ __forceinline__ float lo_of<float>(float) { return 0.0f; }
 template <> __device__ __forceinline__ float lo_of<float2>(float2 v) { return v.y; }
 
-constexpr int SPLIT_THREADS = 128;
+constexpr int SPLIT_THREADS = 128;   // one CTA per row
+constexpr int SPLIT_U = 4;           // loads in flight per thread in the max reduction
 
 // The CTA splits one row: n values, zero-padded to np (a multiple of 8).
 // Pass 1 reduces max |x|; pass 2 handles 8 consecutive elements per thread and
@@ -514,7 +519,17 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     __shared__ float red[SPLIT_THREADS / 32];
     __shared__ int s_e;
     float m = 0.0f;
-    for (int k = threadIdx.x; k < n; k += SPLIT_THREADS) m = fmaxf(m, fabsf(hi_of(row[k])));
+    for (int base = 0; base < n; base += SPLIT_THREADS * SPLIT_U) {
+        float t[SPLIT_U];
+#pragma unroll
+        for (int u = 0; u < SPLIT_U; ++u) {
+            const int k = base + u * SPLIT_THREADS + threadIdx.x;
+            t[u] = (k < n) ? fabsf(hi_of(row[k])) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < SPLIT_U; ++u) m = fmaxf(m, t[u]);
+    }
+#pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
     __syncthreads();
@@ -523,8 +538,8 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
         for (int w = 0; w < SPLIT_THREADS / 32; ++w) mm = fmaxf(mm, red[w]);
         int e = 0;
         if (mm > 0.0f) {
-            float fr = frexpf(mm, &e);       // mm = fr 2^e, fr in [0.5, 1)
-            if (fr == 0.5f) e -= 1;          // scaled |hi| <= 1, hence |F0| <= 1
+            const float fr = frexpf(mm, &e);   // mm = fr 2^e, fr in [0.5, 1)
+            if (fr == 0.5f) e -= 1;            // scaled |hi| <= 1, hence |F0| <= 1
         }
         s_e = e;
         *xexp = e;
@@ -545,8 +560,8 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
             float h = 0.0f, l = 0.0f;
             if (k < n) {
                 const T v = row[k];
-                h = ldexpf(hi_of(v), -e);
-                l = ldexpf(lo_of(v), -e);
+                h = scale2(hi_of(v), -e);   // exact: a power-of-two scaling
+                l = scale2(lo_of(v), -e);
             }
             const float x0 = rintf(h * SC) * ISC;
             const float r = (h - x0) * SC + l * SC;
@@ -573,6 +588,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__re
     const int b = blockIdx.x;
     split_row<T>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
                  G ? G + (size_t)b * ldg : nullptr, a00);
+    leg_griddep_trigger();   // after this CTA's stores: the GEMM's setup may start
 }
 
 // Ragged batch: function i (one CTA) goes to row row[i] of bucket bucket[i].
@@ -587,6 +603,17 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float
     const int r = row[i];
     split_row<float>(f_packed + in_off[i], b.K, b.Kp, b.in.base + (size_t)r * b.in.ld, b.in.pstride,
                      b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00);
+    leg_griddep_trigger();
+}
+
+template <class T>
+int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 *G, int ldg, double a00, int B,
+               cudaStream_t st)
+{
+    if (B == 0) return LEG_OK;
+    split_rows_kernel<T><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg, a00);
+    LEG_LAUNCH_CHECK("split_rows_kernel");
+    return LEG_OK;
 }
 
 __global__ void __launch_bounds__(256) bf16_rows_kernel(const float *__restrict__ x, int n, int np,
@@ -733,17 +760,19 @@ int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int nt
     if (rc) return rc;
     const int npairs = ntiles < pairs ? ntiles : pairs;
     cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
+    cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
     at[0].val.clusterDim.x = 2;
     at[0].val.clusterDim.y = 1;
     at[0].val.clusterDim.z = 1;
+    at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;   // overlaps the split's tail
+    at[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.gridDim = dim3(2 * npairs, 1, 1);
     cfg.blockDim = dim3(THREADS, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cfg.attrs = at;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, single, multi, nprob, ntiles, tn, stages, status, limit));
     return LEG_OK;
 }
@@ -861,9 +890,7 @@ int leg_build_split_transposed(leg_plan *p)
 int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const LegSplitIn &in, float2 *G,
                                  int ldg, cudaStream_t st)
 {
-    split_rows_kernel<float><<<B, SPLIT_THREADS, 0, st>>>(f, p->K, p->K, p->Kp, in, G, ldg, p->a00);
-    LEG_LAUNCH_CHECK("split_rows_kernel");
-    return LEG_OK;
+    return split_rows<float>(f, p->K, p->K, p->Kp, in, G, ldg, p->a00, B, st);
 }
 
 int leg_split_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st)
@@ -914,9 +941,9 @@ int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st)
 {
     // Gbar (double-float, B x ldg, rows valid) -> split planes B x npr
     const LegSplitIn in = leg_split_workspace(p);
-    split_rows_kernel<float2><<<B, SPLIT_THREADS, 0, st>>>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows,
-                                                           leg_adj_depth(p), in, nullptr, 0, 0.0);
-    LEG_LAUNCH_CHECK("split_rows_kernel (adjoint)");
+    int rc = split_rows<float2>(static_cast<const float2 *>(p->Gbar), p->ldg, p->rows, leg_adj_depth(p), in, nullptr,
+                                0, 0.0, B, st);
+    if (rc) return rc;
     return split_adj_gemm(p, in, df, B, st);
 }
 
@@ -935,8 +962,8 @@ int leg_gemm_split_collapsed_fwd(leg_plan *p, int B, float *c, cudaStream_t st)
 int leg_gemm_split_collapsed_adj(leg_plan *p, const float *dc, void *df, int B, cudaStream_t st)
 {
     const LegSplitIn in = leg_split_workspace(p);
-    split_rows_kernel<float><<<B, SPLIT_THREADS, 0, st>>>(dc, p->N, p->N, leg_adj_depth(p), in, nullptr, 0, 0.0);
-    LEG_LAUNCH_CHECK("split_rows_kernel (collapsed adjoint)");
+    int rc = split_rows<float>(dc, p->N, p->N, leg_adj_depth(p), in, nullptr, 0, 0.0, B, st);
+    if (rc) return rc;
     return split_adj_gemm(p, in, df, B, st);
 }
 

@@ -40,7 +40,17 @@ int leg_set_error(int code, const std::string &msg);
 // ---------------------------------------------------------------------------
 static inline int leg_round_up(int x, int m) { return (x + m - 1) / m * m; }
 
-constexpr int LEG_KPAD = 64;      // K is padded to a multiple of this for tensor-core planes
+// Programmatic dependent launch.  A kernel launched with
+// cudaLaunchAttributeProgrammaticStreamSerialization may start before the
+// previous kernel on its stream has finished; leg_griddep_wait() returns once
+// that kernel has completed and its memory is visible, so every thread calls
+// it before touching the previous kernel's output.  leg_griddep_trigger()
+// lets the next such kernel start early.  Both are no-ops for kernels launched
+// without the attribute.
+__device__ __forceinline__ void leg_griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void leg_griddep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+constexpr int LEG_KPAD = 32;      // K is padded to a multiple of this (one 32-wide K block of the tensor-core GEMMs)
 constexpr int LEG_MAX_M = 32768;
 constexpr int LEG_MAX_K = 16385;
 
