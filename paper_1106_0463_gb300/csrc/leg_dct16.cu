@@ -41,6 +41,8 @@ template <> struct Fa<double> {
     static __device__ __forceinline__ T half(T a) { return 0.5 * a; }
     static __device__ __forceinline__ T norm(T a) { return a; }
     static __device__ __forceinline__ T cst(double v) { return v; }
+    static __device__ __forceinline__ T of_int(int v) { return (double)v; }
+    static __device__ __forceinline__ T of_float(float v) { return (double)v; }
     static __device__ __forceinline__ T zero() { return 0.0; }
     static __device__ __forceinline__ T pow2(T a, int e) { return ldexp(a, e); }
 };
@@ -72,13 +74,25 @@ template <> struct Fa<dfl> {
         const float s = a.hi + a.lo;
         return {s, a.lo - (s - a.hi)};
     }
+    // compile-time constants only (the FP64 arithmetic folds away)
     static __device__ __forceinline__ T cst(double v)
     {
         const float h = (float)v;
         return {h, (float)(v - (double)h)};
     }
+    // exact for |v| < 2^24 and for FP32 values: no FP64 instruction at run time
+    static __device__ __forceinline__ T of_int(int v) { return {__int2float_rn(v), 0.0f}; }
+    static __device__ __forceinline__ T of_float(float v) { return {v, 0.0f}; }
     static __device__ __forceinline__ T zero() { return {0.0f, 0.0f}; }
-    static __device__ __forceinline__ T pow2(T a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
+    // a 2^e: one exact multiply per part while 2^e is a normal float
+    static __device__ __forceinline__ T pow2(T a, int e)
+    {
+        if (e >= -126 && e <= 127) {
+            const float m = __int_as_float((e + 127) << 23);
+            return {a.hi * m, a.lo * m};
+        }
+        return {ldexpf(a.hi, e), ldexpf(a.lo, e)};
+    }
 };
 
 template <class R> using CxT = Cx<typename Fa<R>::T>;
@@ -435,6 +449,10 @@ template <> struct GIn<dfl> {
     }
 };
 
+// a cotangent value (FP64, or FP32 for the double-float path) in the arithmetic type
+template <class R> __device__ __forceinline__ typename Fa<R>::T in_of(double v) { return Fa<R>::cst(v); }
+template <class R> __device__ __forceinline__ typename Fa<R>::T in_of(float v) { return Fa<R>::of_float(v); }
+
 __device__ __forceinline__ double out_of(double a) { return a; }
 __device__ __forceinline__ float out_of(dfl a) { return a.hi + a.lo; }
 
@@ -485,7 +503,7 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_f
     constexpr int SHIFT = -(LOG2H + 2);   // 1 / M
     for (int n = t; n < nn; n += D::T) {
         const T_ a = F::pow2(F::sub(Xs[D::px(n)], Xs[D::px(n + 1)]), SHIFT);
-        cf[n] = out_of(F::norm(F::mul(F::cst((double)(2 * n + 1)), a)));
+        cf[n] = out_of(F::norm(F::mul(F::of_int(2 * n + 1), a)));
     }
 }
 
@@ -510,8 +528,8 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
     auto load = [&](int n) -> T_ {
         if (n > N) return F::zero();
         T_ x = F::zero();
-        if (n < N) x = F::mul(F::cst((double)(2 * n + 1)), F::cst((double)vf[n]));
-        if (n >= 1) x = F::sub(x, F::mul(F::cst((double)(2 * n - 1)), F::cst((double)vf[n - 1])));
+        if (n < N) x = F::mul(F::of_int(2 * n + 1), in_of<R>(vf[n]));
+        if (n >= 1) x = F::sub(x, F::mul(F::of_int(2 * n - 1), in_of<R>(vf[n - 1])));
         return x;
     };
     dct16<R, LOG2H>(buf, wsum, t, tw, load);
