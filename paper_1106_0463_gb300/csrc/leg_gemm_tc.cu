@@ -507,14 +507,14 @@ template <> __device__ __forceinline__ float lo_of<float>(float) { return 0.0f; 
 template <> __device__ __forceinline__ float lo_of<float2>(float2 v) { return v.y; }
 
 constexpr int SPLIT_THREADS = 128;   // one CTA per row
-constexpr int SPLIT_U = 4;           // loads in flight per thread in the max reduction
+constexpr int SPLIT_U = 16;          // loads in flight per thread in the max reduction
 
 // The CTA splits one row: n values, zero-padded to np (a multiple of 8).
 // Pass 1 reduces max |x|; pass 2 handles 8 consecutive elements per thread and
 // writes each plane's 8 FP16 values as one 16-byte store.
 template <class T>
 __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
-                                          size_t pstride, int *__restrict__ xexp, float2 *g0, double a00)
+                                          size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00)
 {
     __shared__ float red[SPLIT_THREADS / 32];
     __shared__ int s_e;
@@ -543,14 +543,18 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
         }
         s_e = e;
         *xexp = e;
-        if (g0) {
-            const double v = (double)hi_of(row[0]) * a00;
-            const float h = __double2float_rn(v);
-            *g0 = make_float2(h, __double2float_rn(v - (double)h));
-        }
     }
     __syncthreads();
     const int e = s_e;
+    if (g0 && threadIdx.x == 32) {
+        // a00 x[0] as a double-float pair (a00 = hi + lo; x[0] is FP32): exact
+        // product of the leading parts by FMA, the rest in FP32
+        const float x = hi_of(row[0]);
+        const float p = x * a00.x;
+        const float q = fmaf(x, a00.x, -p) + x * a00.y;
+        const float h = p + q;
+        *g0 = make_float2(h, q - (h - p));
+    }
     constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
     for (int c = threadIdx.x; c < np / 8; c += SPLIT_THREADS) {
         __align__(16) __half o[LEG_SPLIT_NF][8];
@@ -583,7 +587,7 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
 
 template <class T>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
-                                                                   LegSplitIn in, float2 *G, int ldg, double a00)
+                                                                   LegSplitIn in, float2 *G, int ldg, float2 a00)
 {
     const int b = blockIdx.x;
     split_row<T>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
@@ -611,7 +615,9 @@ int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 
                cudaStream_t st)
 {
     if (B == 0) return LEG_OK;
-    split_rows_kernel<T><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg, a00);
+    const float ah = (float)a00;
+    split_rows_kernel<T><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg,
+                                                      make_float2(ah, (float)(a00 - (double)ah)));
     LEG_LAUNCH_CHECK("split_rows_kernel");
     return LEG_OK;
 }

@@ -160,7 +160,7 @@ struct LegRaggedBucket {
     LegSplitIn in;       // B_b x Kp split planes
     float2 *G;           // B_b x ldg double-float G (row 0 written by the split)
     int ldg;
-    double a00;
+    float2 a00;          // the plan's a00 as a double-float pair (hi, lo)
     int K, Kp;
 };
 

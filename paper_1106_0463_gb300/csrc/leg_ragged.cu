@@ -233,7 +233,8 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         bk[p].in.fexp = r->fexp[p];
         bk[p].G = r->G[p];
         bk[p].ldg = r->ldg[p];
-        bk[p].a00 = pl->a00;
+        const float ah = (float)pl->a00;
+        bk[p].a00 = make_float2(ah, (float)(pl->a00 - (double)ah));
         bk[p].K = pl->K;
         bk[p].Kp = pl->Kp;
         if (B > 0) {
