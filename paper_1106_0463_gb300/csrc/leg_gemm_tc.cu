@@ -510,24 +510,56 @@ constexpr int SPLIT_THREADS = 128;   // one CTA per row
 constexpr int SPLIT_U = 16;          // loads in flight per thread in the max reduction
 
 // The CTA splits one row: n values, zero-padded to np (a multiple of 8).
-// Pass 1 reduces max |x|; pass 2 handles 8 consecutive elements per thread and
-// writes each plane's 8 FP16 values as one 16-byte store.
-template <class T>
+// Pass 1 reduces max |x| with coalesced loads (SPLIT_U in flight per thread)
+// and, with STAGE, keeps the row in shared memory (n values of T); pass 2
+// handles 8 consecutive elements per thread, read back from shared memory
+// (or again from global memory without STAGE), and writes each plane's 8 FP16
+// values as one 16-byte store.
+template <class T> __device__ __forceinline__ T zero_of();
+template <> __device__ __forceinline__ float zero_of<float>() { return 0.0f; }
+template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.0f, 0.0f); }
+
+// Planes of two scaled values (h, l: leading and trailing parts of x 2^-e)
+// as FP16 pairs: the seven planes' values for elements i and i + 1.
+__device__ __forceinline__ void split_pair(float ha, float la, float hb, float lb, __half2 (&o)[LEG_SPLIT_NF])
+{
+    constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
+    const float x0a = rintf(ha * SC) * ISC, x0b = rintf(hb * SC) * ISC;
+    const float ra = (ha - x0a) * SC + la * SC, rb = (hb - x0b) * SC + lb * SC;
+    const __half2 f1 = __floats2half2_rn(ra, rb);
+    const float2 f1f = __half22float2(f1);
+    const float da = ra - f1f.x, db = rb - f1f.y;
+    o[0] = __floats2half2_rn(x0a, x0b);
+    o[1] = f1;
+    o[2] = __floats2half2_rn(da, db);
+    o[3] = __floats2half2_rn(f1f.x * ISC, f1f.y * ISC);
+    o[4] = __floats2half2_rn(x0a * ISC, x0b * ISC);
+    o[5] = __floats2half2_rn(f1f.x * (ISC * ISC), f1f.y * (ISC * ISC));
+    o[6] = __floats2half2_rn(da * ISC, db * ISC);
+}
+
+template <class T, bool STAGE>
 __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
                                           size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00)
 {
     __shared__ float red[SPLIT_THREADS / 32];
     __shared__ int s_e;
+    extern __shared__ __align__(16) unsigned char split_smem[];
+    T *xs = reinterpret_cast<T *>(split_smem);   // STAGE: np values, zero beyond n
     float m = 0.0f;
-    for (int base = 0; base < n; base += SPLIT_THREADS * SPLIT_U) {
-        float t[SPLIT_U];
+    for (int base = 0; base < np; base += SPLIT_THREADS * SPLIT_U) {
+        T t[SPLIT_U];
 #pragma unroll
         for (int u = 0; u < SPLIT_U; ++u) {
             const int k = base + u * SPLIT_THREADS + threadIdx.x;
-            t[u] = (k < n) ? fabsf(hi_of(row[k])) : 0.0f;
+            t[u] = (k < n) ? row[k] : zero_of<T>();
         }
 #pragma unroll
-        for (int u = 0; u < SPLIT_U; ++u) m = fmaxf(m, t[u]);
+        for (int u = 0; u < SPLIT_U; ++u) {
+            m = fmaxf(m, fabsf(hi_of(t[u])));
+            const int k = base + u * SPLIT_THREADS + threadIdx.x;
+            if (STAGE && k < np) xs[k] = t[u];
+        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
@@ -549,35 +581,33 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     if (g0 && threadIdx.x == 32) {
         // a00 x[0] as a double-float pair (a00 = hi + lo; x[0] is FP32): exact
         // product of the leading parts by FMA, the rest in FP32
-        const float x = hi_of(row[0]);
+        const float x = hi_of(STAGE ? xs[0] : row[0]);
         const float p = x * a00.x;
         const float q = fmaf(x, a00.x, -p) + x * a00.y;
         const float h = p + q;
         *g0 = make_float2(h, q - (h - p));
     }
-    constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
+    // x 2^-e: one exact multiply while 2^-e is a normal float (ldexpf beyond)
+    const bool mul_ok = (-e >= -126 && -e <= 127);
+    const float sc = mul_ok ? __int_as_float((127 - e) << 23) : 0.0f;
     for (int c = threadIdx.x; c < np / 8; c += SPLIT_THREADS) {
-        __align__(16) __half o[LEG_SPLIT_NF][8];
+        float h[8], l[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = 8 * c + i;
-            float h = 0.0f, l = 0.0f;
-            if (k < n) {
-                const T v = row[k];
-                h = scale2(hi_of(v), -e);   // exact: a power-of-two scaling
-                l = scale2(lo_of(v), -e);
-            }
-            const float x0 = rintf(h * SC) * ISC;
-            const float r = (h - x0) * SC + l * SC;
-            const __half f1 = __float2half_rn(r);
-            const float f1f = __half2float(f1);
-            o[0][i] = __float2half_rn(x0);
-            o[1][i] = f1;
-            o[2][i] = __float2half_rn(r - f1f);
-            o[3][i] = __float2half_rn(f1f * ISC);
-            o[4][i] = __float2half_rn(x0 * ISC);
-            o[5][i] = __float2half_rn(f1f * (ISC * ISC));
-            o[6][i] = __float2half_rn((r - f1f) * ISC);
+            T v = zero_of<T>();
+            if (STAGE) v = xs[k];                 // zero-padded: no bound check
+            else if (k < n) v = row[k];
+            h[i] = mul_ok ? hi_of(v) * sc : ldexpf(hi_of(v), -e);
+            l[i] = mul_ok ? lo_of(v) * sc : ldexpf(lo_of(v), -e);
+        }
+        __align__(16) __half2 o[LEG_SPLIT_NF][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 q[LEG_SPLIT_NF];
+            split_pair(h[2 * i], l[2 * i], h[2 * i + 1], l[2 * i + 1], q);
+#pragma unroll
+            for (int p = 0; p < LEG_SPLIT_NF; ++p) o[p][i] = q[p];
         }
 #pragma unroll
         for (int p = 0; p < LEG_SPLIT_NF; ++p)
@@ -585,17 +615,19 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     }
 }
 
-template <class T>
+template <class T, bool STAGE>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
                                                                    LegSplitIn in, float2 *G, int ldg, float2 a00)
 {
     const int b = blockIdx.x;
-    split_row<T>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
-                 G ? G + (size_t)b * ldg : nullptr, a00);
+    split_row<T, STAGE>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
+                        G ? G + (size_t)b * ldg : nullptr, a00);
     leg_griddep_trigger();   // after this CTA's stores: the GEMM's setup may start
 }
 
-// Ragged batch: function i (one CTA) goes to row row[i] of bucket bucket[i].
+// Ragged batch: function i (one CTA) goes to row row[i] of bucket bucket[i];
+// with STAGE the dynamic shared memory holds the longest row.
+template <bool STAGE>
 __global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float *__restrict__ f_packed,
                                                                      const long long *__restrict__ in_off,
                                                                      const int *__restrict__ bucket,
@@ -605,10 +637,13 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float
     const int i = blockIdx.x;
     const LegRaggedBucket &b = bk[bucket[i]];
     const int r = row[i];
-    split_row<float>(f_packed + in_off[i], b.K, b.Kp, b.in.base + (size_t)r * b.in.ld, b.in.pstride,
-                     b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00);
+    split_row<float, STAGE>(f_packed + in_off[i], b.K, b.Kp, b.in.base + (size_t)r * b.in.ld, b.in.pstride,
+                           b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00);
     leg_griddep_trigger();
 }
+
+// Rows of at most this many bytes are staged in shared memory by the split.
+constexpr size_t SPLIT_STAGE_MAX = 16384;
 
 template <class T>
 int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 *G, int ldg, double a00, int B,
@@ -616,8 +651,12 @@ int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 
 {
     if (B == 0) return LEG_OK;
     const float ah = (float)a00;
-    split_rows_kernel<T><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg,
-                                                      make_float2(ah, (float)(a00 - (double)ah)));
+    const float2 a00p = make_float2(ah, (float)(a00 - (double)ah));
+    const size_t bytes = ((size_t)np * sizeof(T) + 15) / 16 * 16;
+    if (bytes <= SPLIT_STAGE_MAX)
+        split_rows_kernel<T, true><<<B, SPLIT_THREADS, bytes, st>>>(x, ldx, n, np, in, G, ldg, a00p);
+    else
+        split_rows_kernel<T, false><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg, a00p);
     LEG_LAUNCH_CHECK("split_rows_kernel");
     return LEG_OK;
 }
@@ -1007,10 +1046,14 @@ int leg_gemm_split_grouped(const TcProblem *d_probs, int nprob, int ntiles, int 
 }
 
 int leg_split_ragged(const float *f_packed, const long long *in_off, const int *bucket, const int *row,
-                     const LegRaggedBucket *bk, int count, cudaStream_t st)
+                     const LegRaggedBucket *bk, int count, int max_k, cudaStream_t st)
 {
     if (count == 0) return LEG_OK;
-    split_ragged_kernel<<<count, SPLIT_THREADS, 0, st>>>(f_packed, in_off, bucket, row, bk);
+    const size_t bytes = ((size_t)leg_round_up(max_k, LEG_KPAD) * sizeof(float) + 15) / 16 * 16;
+    if (bytes <= SPLIT_STAGE_MAX)
+        split_ragged_kernel<true><<<count, SPLIT_THREADS, bytes, st>>>(f_packed, in_off, bucket, row, bk);
+    else
+        split_ragged_kernel<false><<<count, SPLIT_THREADS, 0, st>>>(f_packed, in_off, bucket, row, bk);
     LEG_LAUNCH_CHECK("split_ragged_kernel");
     return LEG_OK;
 }

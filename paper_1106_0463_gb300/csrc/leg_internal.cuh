@@ -225,7 +225,7 @@ int leg_split_problem_tiles(const TcProblem &pr);
 int leg_gemm_split_grouped(const TcProblem *d_probs, int nprob, int ntiles, int tn, int *status, long long limit,
                            cudaStream_t st);
 int leg_split_ragged(const float *f_packed, const long long *in_off, const int *bucket, const int *row,
-                     const LegRaggedBucket *bk, int count, cudaStream_t st);
+                     const LegRaggedBucket *bk, int count, int max_k, cudaStream_t st);   // max_k: longest row
 int leg_fft_forward_ragged(const leg_plan *p, const void *G, int ldg, float *c_packed, int B, const int *rowfn,
                            const long long *out_off, const int *n_out, cudaStream_t st);
 int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const LegSplitIn &in, float2 *G,

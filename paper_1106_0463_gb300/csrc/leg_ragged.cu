@@ -34,6 +34,7 @@ struct leg_ragged {
     LegRaggedBucket *d_bk = nullptr;
     TcProblem *d_probs = nullptr;
     int nprob = 0, ntiles = 0, tn = 128;
+    int max_k = 0;   // longest row (samples) over the buckets
     int *status = nullptr;
     long long wait_limit = 2000000000LL;
     cudaStream_t rs = nullptr;
@@ -78,7 +79,7 @@ int upload(T **dst, const T *src, size_t n)
 
 int enqueue(leg_ragged *r, const float *f, float *c, cudaStream_t st)
 {
-    int rc = leg_split_ragged(f, r->d_in_off, r->d_bucket, r->d_row, r->d_bk, r->count, st);
+    int rc = leg_split_ragged(f, r->d_in_off, r->d_bucket, r->d_row, r->d_bk, r->count, r->max_k, st);
     if (rc) return rc;
     if ((rc = leg_gemm_split_grouped(r->d_probs, r->nprob, r->ntiles, r->tn, r->status, r->wait_limit, st))) return rc;
     for (int p = 0; p < r->nplans; ++p) {
@@ -237,6 +238,7 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         bk[p].a00 = make_float2(ah, (float)(pl->a00 - (double)ah));
         bk[p].K = pl->K;
         bk[p].Kp = pl->Kp;
+        if (pl->K > r->max_k) r->max_k = pl->K;
         if (B > 0) {
             TcProblem pr;
             if ((rc = leg_make_split_problem(&pr, pl, bk[p].in, B, r->G[p], r->ldg[p], tn))) return fail(rc);
