@@ -377,7 +377,8 @@ def gpu_arm(args, rank, world, local_rank):
     value = whole_job_rate(world, B * N, ms_per_step)
     prep_ms, gemm_ms, fft_ms = (float(v) for v in stage.mean(0))
 
-    # ---------------- e2e through the public API with pinned host buffers
+    # ---------------- e2e through the public API with pinned host buffers:
+    # leg_forward_host copies f in and c out, overlapped with the computation
     plan, f, c = res["plan"], res["f"], res["c"]
     f_host = torch.from_numpy(res["f_np"]).to(f.dtype).pin_memory()
     c_host = torch.empty(c.shape, dtype=c.dtype).pin_memory()
@@ -387,17 +388,30 @@ def gpu_arm(args, rank, world, local_rank):
         flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(st)
-        f.copy_(f_host, non_blocking=True)
-        plan.forward(f, c)
-        c_host.copy_(c, non_blocking=True)
+        plan.forward_host(f_host, c_host, sync=False)
         e1.record(st)
         e1.synchronize()
         if i >= args.warmup:
             e2e_ms.append(e0.elapsed_time(e1))
+    # the bare copies, for reference (not part of the e2e number)
+    copy_ms = {}
+    for direction, dst, src in (("h2d", f, f_host), ("d2h", c_host, c)):
+        ts = []
+        for i in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            dst.copy_(src, non_blocking=True)
+            e1.record(st)
+            e1.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        copy_ms[direction] = statistics.mean(ts)
     e2e_step = max_over_ranks(torch, dist, statistics.mean(e2e_ms), "cuda")
     e2e = {"value": whole_job_rate(world, B * N, e2e_step), "unit": UNIT,
            "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
-           "d2h_bytes_per_step": c_host.numel() * c_host.element_size()}
+           "d2h_bytes_per_step": c_host.numel() * c_host.element_size(),
+           "api": "leg_forward_host (pinned host buffers, copies overlapped with the kernels)",
+           "ms_per_step": e2e_step, "bare_copy_ms": copy_ms}
 
     if rank != 0:
         if dist is not None:

@@ -296,7 +296,7 @@ LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cu
  * GEMM result) come from one static device array of 64 MiB in the library,
  * which every GPU that loads the library keeps reserved until process exit.
  * A batch needing more scratch than that (about B*(14*Kp + 8*Mr) bytes, Kp = K
- * rounded up to 64, Mr = M/2+1 rounded up to 64) is rejected with
+ * rounded up to 32, Mr = M/2+1 rounded up to 32) is rejected with
  * LEG_ERR_INVALID_ARG and a message stating the sizes.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  All calls
@@ -304,6 +304,26 @@ LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cu
  * overlaps on the GPU race on it, so serialise them.
  */
 LEG_API int leg_forward_noalloc(leg_plan_t plan, const float *f, float *c, int B, cudaStream_t stream);
+
+/*
+ * leg_forward_host -- leg_forward on HOST buffers: the batch is copied to the
+ * device, transformed and copied back, with the copies overlapped with the
+ * computation.  (A library convenience with no counterpart in the paper.)
+ *   f_host  host, B x K (FP64 for LEG_F64, FP32 otherwise), row-major;
+ *   c_host  host, B x N (same type); overwritten.
+ * For LEG_SPLIT_FP16 plans the input goes over in four pieces on an internal
+ * stream and the split of each piece starts when it has landed; the
+ * coefficients come back per piece while the next piece is transformed.
+ * Results equal leg_forward's bit for bit.  Ordered after the work already on
+ * `stream`; c_host is complete once `stream` has reached the end of the call
+ * (synchronise `stream` before reading it); both host buffers must stay valid
+ * until then.  Page-locked host memory (cudaHostAlloc, or a pinned tensor)
+ * lets the copies run at full speed and overlap; pageable memory works but
+ * the copies then run through a staging buffer.  The plan keeps device
+ * copies of the largest batch it has seen (B x (K + N) values) and two
+ * internal streams; growing them synchronises the device.
+ */
+LEG_API int leg_forward_host(leg_plan_t plan, const void *f_host, void *c_host, int B, cudaStream_t stream);
 
 /* Message for the most recent failing call on this host thread ("" if none). */
 LEG_API const char *leg_last_error(void);

@@ -70,6 +70,7 @@ def _load():
         "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_backward": ([vp, vp, vp, i, vp], i),
         "leg_forward_noalloc": ([vp, vp, vp, i, vp], i),
+        "leg_forward_host": ([vp, vp, vp, i, vp], i),
         "leg_plain_forward": ([vp, i, vp, i, vp, vp], i),
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
@@ -123,6 +124,18 @@ def _stream(stream) -> ctypes.c_void_p:
 def _dev_tensor(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
         raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _host_tensor(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cpu":
+        raise ValueError("%s must be a CPU tensor" % name)
     if t.dtype != dtype:
         raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
     if tuple(t.shape) != tuple(shape):
@@ -226,6 +239,24 @@ class Plan:
         pc = _dev_tensor(c, torch.float32, (B, self.N), "c")
         _check(_lib.leg_forward_noalloc(self._h, pf, pc, B, _stream(stream)))
         return c
+
+    def forward_host(self, f_host: torch.Tensor, c_host: torch.Tensor | None = None, stream=None,
+                     sync: bool = True) -> torch.Tensor:
+        """c = L f for host tensors (leg_forward_host): the copies to and from the
+        device overlap the computation.  f_host (B, K) on the CPU, ideally pinned;
+        c_host (B, N) on the CPU (pinned and allocated when None).  With
+        sync=False the call returns at once and c_host is complete when the
+        stream has reached it."""
+        B = f_host.shape[0] if f_host.dim() == 2 else -1
+        pf = _host_tensor(f_host, self.io_dtype, (B, self.K), "f_host")
+        if c_host is None:
+            c_host = torch.empty((B, self.N), dtype=self.io_dtype).pin_memory()
+        pc = _host_tensor(c_host, self.io_dtype, (B, self.N), "c_host")
+        st = _stream(stream)
+        _check(_lib.leg_forward_host(self._h, pf, pc, B, st))
+        if sync:
+            (stream or torch.cuda.current_stream()).synchronize()
+        return c_host
 
     def forward_profiled(self, f: torch.Tensor, c: torch.Tensor, stream=None):
         """Forward pass timed per stage (leg_forward_profiled); synchronises.

@@ -29,6 +29,7 @@ void free_workspace(leg_plan *p)
 void free_plan(leg_plan *p)
 {
     if (!p) return;
+    leg_host_free(p);
     free_workspace(p);
     cudaFree(p->omt2);
     cudaFree(p->wq);

@@ -344,10 +344,11 @@ __device__ __forceinline__ typename Fa<R>::T fn_sum(typename Fa<R>::T v, int t, 
 
 // X_0..X_L of the L+1 values delivered by load(j) (the caller's element type
 // converted to the arithmetic type), left in Xs[D::px(n)], n = 0..L (a real
-// view of buf).
+// view of buf).  Only X_0..X_{2 kmax + 1} and X_L are exact: the
+// recombination skips k > kmax (kmax = H - 1 for all of them).
 template <class R, int LOG2H, class Load>
 __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int t, const typename Ar<R>::TW *tw,
-                                      Load load)
+                                      int kmax, Load load)
 {
     using D = D16<LOG2H>;
     using F = Fa<R>;
@@ -383,6 +384,9 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
         fft_pass_any<R, LOG2H>(P0, v, buf, t, 1, tw);
         Ns = P0;
     }
+    // one copy of the pass body (runtime Ns and radix): fully unrolled passes
+    // of double-float butterflies outgrow the instruction cache
+#pragma unroll 1
     while (Ns < H) {
         fsync<T>();
 #pragma unroll
@@ -399,13 +403,17 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
 #pragma unroll
     for (int i = 0; i < E; ++i) {
         const int k = t + i * T;
-        const CxT<R> za = buf[D::pc(k)], zb = buf[D::pc((H - k) & (H - 1))];
-        T_ c, s;
-        twid(tw, 2 * k, c, s);                 // e^{2 pi i k / L}
-        const T_ sre = F::add(za.re, zb.re), dre = F::sub(za.re, zb.re);
-        const T_ sim = F::add(za.im, zb.im), dim = F::sub(za.im, zb.im);
-        ry[i] = F::norm(F::add(sre, F::add(F::mul(c, sim), F::mul(s, dre))));
-        iy[i] = (k == 0) ? F::zero() : F::norm(F::add(dim, F::sub(F::mul(s, sim), F::mul(c, dre))));
+        ry[i] = F::zero();
+        iy[i] = F::zero();
+        if (k <= kmax) {                       // outputs above X_{2 kmax + 1} are not wanted
+            const CxT<R> za = buf[D::pc(k)], zb = buf[D::pc((H - k) & (H - 1))];
+            T_ c, s;
+            twid(tw, 2 * k, c, s);             // e^{2 pi i k / L}
+            const T_ sre = F::add(za.re, zb.re), dre = F::sub(za.re, zb.re);
+            const T_ sim = F::add(za.im, zb.im), dim = F::sub(za.im, zb.im);
+            ry[i] = F::norm(F::add(sre, F::add(F::mul(c, sim), F::mul(s, dre))));
+            if (k != 0) iy[i] = F::norm(F::add(dim, F::sub(F::mul(s, sim), F::mul(c, dre))));
+        }
     }
     T_ xL = F::zero();
     if (t == T - 1) {
@@ -490,7 +498,9 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_f
     }
     fsync<D::T>();
     const GT *g = reinterpret_cast<const GT *>(buf);
-    dct16<R, LOG2H>(buf, wsum, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
+    // c_n for n < N reads X_0..X_N: X_2k for k <= N/2 and X_2k+1 for k <= (N-1)/2
+    const int kmax = min(D::H - 1, N / 2);
+    dct16<R, LOG2H>(buf, wsum, t, tw, kmax, [&](int j) -> T_ { return GIn<R>::get(g, j); });
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
     typename Ar<R>::OUT *cf = c + (size_t)f * N;
@@ -532,7 +542,7 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
         if (n >= 1) x = F::sub(x, F::mul(F::of_int(2 * n - 1), in_of<R>(vf[n - 1])));
         return x;
     };
-    dct16<R, LOG2H>(buf, wsum, t, tw, load);
+    dct16<R, LOG2H>(buf, wsum, t, tw, D::H - 1, load);
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
     const T_ x0 = load(0), xL = load(L);

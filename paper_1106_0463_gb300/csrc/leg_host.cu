@@ -1,0 +1,148 @@
+// leg_forward_host: leg_forward on host buffers.  The batch is copied to the
+// device, transformed and copied back with the copies overlapped with the
+// computation: for the split-FP16 path the host-to-device copy runs in
+// LEG_HOST_CHUNKS pieces on an internal stream and the input split of each
+// piece starts as soon as it has landed; the transform runs per piece and
+// each piece's coefficients are copied back while the next piece is
+// transformed.  The Abel GEMM (or the collapsed GEMM) runs once on the whole
+// batch in between.  Results are the same as leg_forward's bit for bit: every
+// kernel computes each function independently of the others.
+#include <new>
+
+#include "leg_internal.cuh"
+
+struct LegHostState {
+    void *f = nullptr, *c = nullptr;   // device copies of the batch (input, output)
+    int cap = 0;                       // functions they hold
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr;
+    cudaEvent_t in[LEG_HOST_CHUNKS] = {}, out[LEG_HOST_CHUNKS] = {};
+};
+
+void leg_host_free(leg_plan *p)
+{
+    LegHostState *h = p->host;
+    if (!h) return;
+    cudaFree(h->f);
+    cudaFree(h->c);
+    for (int i = 0; i < LEG_HOST_CHUNKS; ++i) {
+        if (h->in[i]) cudaEventDestroy(h->in[i]);
+        if (h->out[i]) cudaEventDestroy(h->out[i]);
+    }
+    if (h->start) cudaEventDestroy(h->start);
+    if (h->done) cudaEventDestroy(h->done);
+    if (h->h2d) cudaStreamDestroy(h->h2d);
+    if (h->d2h) cudaStreamDestroy(h->d2h);
+    delete h;
+    p->host = nullptr;
+}
+
+namespace {
+
+int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
+{
+    if (!p->host) {
+        LegHostState *h = new (std::nothrow) LegHostState();
+        if (!h) return leg_set_error(LEG_ERR_OOM, "host allocation of the copy state failed");
+        p->host = h;
+        LEG_CUDA_TRY(cudaStreamCreateWithFlags(&h->h2d, cudaStreamNonBlocking));
+        LEG_CUDA_TRY(cudaStreamCreateWithFlags(&h->d2h, cudaStreamNonBlocking));
+        LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->start, cudaEventDisableTiming));
+        LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->done, cudaEventDisableTiming));
+        for (int i = 0; i < LEG_HOST_CHUNKS; ++i) {
+            LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->in[i], cudaEventDisableTiming));
+            LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->out[i], cudaEventDisableTiming));
+        }
+    }
+    LegHostState *h = p->host;
+    if (B > h->cap) {
+        LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
+        cudaFree(h->f);
+        cudaFree(h->c);
+        h->f = h->c = nullptr;
+        h->cap = 0;
+        LEG_CUDA_TRY(cudaMalloc(&h->f, eb * (size_t)B * p->K));
+        LEG_CUDA_TRY(cudaMalloc(&h->c, eb * (size_t)B * p->N));
+        h->cap = B;
+    }
+    *out = h;
+    return LEG_OK;
+}
+
+}  // namespace
+
+extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, int B, cudaStream_t st)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (B < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0");
+    if (B == 0) return LEG_OK;
+    if (!f_host || !c_host) return leg_set_error(LEG_ERR_INVALID_ARG, "null f_host or c_host");
+    int dev = -1;
+    LEG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device) return leg_set_error(LEG_ERR_INVALID_ARG, "current device differs from the plan's device");
+    const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
+    int rc = leg_plan_reserve(p, B);
+    if (rc) return rc;
+    LegHostState *h = nullptr;
+    if ((rc = host_state(p, B, eb, &h))) return rc;
+
+    const bool split = (p->dtype == LEG_SPLIT_FP16);
+    const int nch = split ? (B < LEG_HOST_CHUNKS ? B : LEG_HOST_CHUNKS) : 1;
+    auto off = [&](int i) { return (int)((long long)B * i / nch); };
+    const size_t frow = eb * p->K, crow = eb * p->N;
+    const char *fh = static_cast<const char *>(f_host);
+    char *ch = static_cast<char *>(c_host);
+    char *fd = static_cast<char *>(h->f), *cd = static_cast<char *>(h->c);
+
+    // the copies start after the work already queued on `stream` (which may
+    // still read the device buffers of an earlier call)
+    LEG_CUDA_TRY(cudaEventRecord(h->start, st));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(h->h2d, h->start, 0));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->start, 0));
+    for (int i = 0; i < nch; ++i) {
+        const int b0 = off(i), nb = off(i + 1) - b0;
+        LEG_CUDA_TRY(cudaMemcpyAsync(fd + frow * b0, fh + frow * b0, frow * nb, cudaMemcpyHostToDevice, h->h2d));
+        LEG_CUDA_TRY(cudaEventRecord(h->in[i], h->h2d));
+    }
+    if (split) {
+        const LegSplitIn in = leg_split_workspace(p);
+        float2 *G = p->collapsed() ? nullptr : static_cast<float2 *>(p->G);
+        for (int i = 0; i < nch; ++i) {
+            const int b0 = off(i), nb = off(i + 1) - b0;
+            LegSplitIn ini = in;
+            ini.base = in.base + (size_t)b0 * in.ld;
+            ini.fexp = in.fexp + b0;
+            LEG_CUDA_TRY(cudaStreamWaitEvent(st, h->in[i], 0));
+            rc = leg_split_prepare_input_into(p, reinterpret_cast<const float *>(fd + frow * b0), nb, ini,
+                                              G ? G + (size_t)b0 * p->ldg : nullptr, p->ldg, st);
+            if (rc) return rc;
+        }
+        if (p->collapsed()) {
+            if ((rc = leg_gemm_split_collapsed_fwd(p, B, reinterpret_cast<float *>(cd), st))) return rc;
+            LEG_CUDA_TRY(cudaEventRecord(h->out[0], st));
+            LEG_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->out[0], 0));
+            LEG_CUDA_TRY(cudaMemcpyAsync(ch, cd, crow * B, cudaMemcpyDeviceToHost, h->d2h));
+        } else {
+            if ((rc = leg_gemm_split_fwd(p, B, st))) return rc;
+            for (int i = 0; i < nch; ++i) {
+                const int b0 = off(i), nb = off(i + 1) - b0;
+                rc = leg_fft_forward(p, G + (size_t)b0 * p->ldg, p->ldg, cd + crow * b0, nb, st);
+                if (rc) return rc;
+                LEG_CUDA_TRY(cudaEventRecord(h->out[i], st));
+                LEG_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->out[i], 0));
+                LEG_CUDA_TRY(cudaMemcpyAsync(ch + crow * b0, cd + crow * b0, crow * nb, cudaMemcpyDeviceToHost,
+                                             h->d2h));
+            }
+        }
+    } else {
+        LEG_CUDA_TRY(cudaStreamWaitEvent(st, h->in[0], 0));
+        if ((rc = leg_forward(p, fd, cd, B, st))) return rc;
+        LEG_CUDA_TRY(cudaEventRecord(h->out[0], st));
+        LEG_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->out[0], 0));
+        LEG_CUDA_TRY(cudaMemcpyAsync(ch, cd, crow * B, cudaMemcpyDeviceToHost, h->d2h));
+    }
+    // later work on `stream` (and a synchronisation of it) sees c_host complete
+    LEG_CUDA_TRY(cudaEventRecord(h->done, h->d2h));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(st, h->done, 0));
+    return LEG_OK;
+}

@@ -76,6 +76,9 @@ constexpr int LEG_SPLIT_NF = 7;
 // ---------------------------------------------------------------------------
 // Plan.
 // ---------------------------------------------------------------------------
+struct LegHostState;                  // leg_forward_host's device copies, streams, events (leg_host.cu)
+constexpr int LEG_HOST_CHUNKS = 4;     // pieces of a leg_forward_host batch (split-FP16 plans)
+
 struct leg_plan {
     int N, M, K, Q, dtype;
     unsigned flags;
@@ -127,7 +130,10 @@ struct leg_plan {
     __nv_bfloat16 *Fbf = nullptr;                 // bf16 input plane B x Kp
     int *fexp = nullptr;                          // per-function power-of-two scale
     void *Gbar = nullptr;     // backward: B x ldg (FP64 for LEG_F64, FP32 otherwise)
+    LegHostState *host = nullptr;   // created by the first leg_forward_host
 };
+
+void leg_host_free(leg_plan *p);
 
 // Split input planes of a batch: LEG_SPLIT_NF FP16 planes of B rows with row
 // stride ld; plane s starts at base + s * pstride.
