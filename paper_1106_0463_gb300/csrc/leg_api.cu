@@ -29,6 +29,8 @@ void free_workspace(leg_plan *p)
 void free_plan(leg_plan *p)
 {
     if (!p) return;
+    if (p->fwd_exec) cudaGraphExecDestroy(p->fwd_exec);
+    if (p->cap) cudaStreamDestroy(p->cap);
     leg_host_free(p);
     free_workspace(p);
     cudaFree(p->omt2);
@@ -305,9 +307,65 @@ int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, c
 }
 }  // namespace
 
+// Launches of the same call replayed from a CUDA graph: the first call with a
+// key runs directly, the second captures and instantiates, later ones replay.
+// A call made while the caller's stream is itself being captured runs
+// directly (its launches join the caller's graph).
 extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st)
 {
-    return forward_impl(p, f, c, B, st, nullptr);
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B <= 0 || !f || !c) return forward_impl(p, f, c, B, st, nullptr);   // no-op or argument error
+    if ((rc = ensure_workspace(p, B))) return rc;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return forward_impl(p, f, c, B, st, nullptr);
+    leg_plan::GraphKey key;
+    key.f = f;
+    key.c = c;
+    key.B = B;
+    key.wsB = p->ws_B;
+    key.G = p->G;
+    key.Fh = p->Fh;
+    key.tn = p->tn;
+    key.fft = p->fft_variant;
+    key.wait = p->wait_limit;
+    if (p->fwd_exec && key == p->fwd_key) {
+        LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
+        return LEG_OK;
+    }
+    if (p->fwd_exec) {
+        cudaGraphExecDestroy(p->fwd_exec);
+        p->fwd_exec = nullptr;
+    }
+    if (!(p->fwd_seen && key == p->fwd_key)) {
+        p->fwd_key = key;
+        p->fwd_seen = true;
+        return forward_impl(p, f, c, B, st, nullptr);
+    }
+    // second call with this key: capture the launches on the plan's own stream
+    if (!p->cap) LEG_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
+    LEG_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
+    rc = forward_impl(p, f, c, B, p->cap, nullptr);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(p->cap, &g);
+    if (rc || ec != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        p->fwd_seen = false;
+        if (rc) return rc;
+        return forward_impl(p, f, c, B, st, nullptr);   // capture unavailable: run directly
+    }
+    const cudaError_t ei = cudaGraphInstantiateWithFlags(&p->fwd_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        p->fwd_exec = nullptr;
+        p->fwd_seen = false;
+        return forward_impl(p, f, c, B, st, nullptr);
+    }
+    LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
+    return LEG_OK;
 }
 
 extern "C" int leg_forward_profiled(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, float *ms)

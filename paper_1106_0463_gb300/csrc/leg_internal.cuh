@@ -131,6 +131,26 @@ struct leg_plan {
     int *fexp = nullptr;                          // per-function power-of-two scale
     void *Gbar = nullptr;     // backward: B x ldg (FP64 for LEG_F64, FP32 otherwise)
     LegHostState *host = nullptr;   // created by the first leg_forward_host
+
+    // leg_forward replays a CUDA graph of its launches when called again with
+    // the same buffers and launch parameters (the key); captured on `cap`
+    struct GraphKey {
+        const void *f = nullptr;
+        void *c = nullptr;
+        int B = 0, wsB = 0;   // wsB: the workspace's capacity (plane strides depend on it)
+        void *G = nullptr, *Fh = nullptr;
+        int tn = 0, fft = 0;
+        long long wait = 0;
+        bool operator==(const GraphKey &o) const
+        {
+            return f == o.f && c == o.c && B == o.B && wsB == o.wsB && G == o.G && Fh == o.Fh && tn == o.tn &&
+                   fft == o.fft && wait == o.wait;
+        }
+    };
+    GraphKey fwd_key;
+    bool fwd_seen = false;                 // the key's launches ran once directly
+    cudaGraphExec_t fwd_exec = nullptr;
+    cudaStream_t cap = nullptr;
 };
 
 void leg_host_free(leg_plan *p);

@@ -68,3 +68,39 @@ def test_split_backward_is_the_transpose(leg, oracle):
     df = plan.backward(torch.from_numpy(v).cuda())
     plan.status()
     assert relerr(df.double().cpu().numpy(), v.astype(np.float64) @ L) < 1e-6
+
+
+@pytest.mark.parametrize("dt,tol", [(3, 1e-6), (0, 1e-11)])
+def test_largest_k_polynomial_input_is_exact(leg, oracle, dt, tol):
+    """K = 16385 samples (513 K blocks of the GEMM) of polynomials of degree
+    1000 with M > N + degree and the exact tau rule: the method has no
+    discretisation error, so the GPU meets the plain definition (route 1)."""
+    N, M, K, B, deg = 512, 2048, 16385, 5, 1000
+    rng = np.random.default_rng(11)
+    coef = np.zeros((B, K))
+    coef[:, :deg + 1] = rng.standard_normal((B, deg + 1)) * 0.995 ** np.arange(deg + 1)
+    f = workloads.chebyshev_values(coef)
+    plan = leg.Plan(N, M, K, 0, dt)
+    io = np.float64 if dt == leg.F64 else np.float32
+    fi = f.astype(io)
+    c = plan.forward(torch.from_numpy(fi).cuda())
+    plan.status()
+    ref = oracle.coeffs_direct(N, (deg + N) // 2 + 4, f_cl=fi.astype(np.float64))
+    assert relerr(c.double().cpu().numpy(), ref) < tol
+
+
+def test_degenerate_inputs(leg, oracle):
+    """All-zero rows give zero coefficients (no NaN from the zero scale), a
+    constant gives c_0 only, and inputs near 1e30 and 1e-30 keep their
+    relative accuracy through the per-function power-of-two scales."""
+    N, M, K = 40, 128, 97
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    base = cheb_inputs(2, K, seed=5)
+    f = np.stack([np.zeros(K), np.full(K, 3.25), base[0] * 1e30, base[1] * 1e-30]).astype(np.float32)
+    c = plan.forward(torch.from_numpy(f).cuda()).double().cpu().numpy()
+    plan.status()
+    assert np.all(np.isfinite(c))
+    assert np.all(c[0] == 0.0)
+    assert abs(c[1, 0] - 3.25) < 1e-6 * 3.25 and np.max(np.abs(c[1, 1:])) < 1e-6 * 3.25
+    ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f[2:].astype(np.float64))
+    assert relerr(c[2:], ref) < 1e-6
