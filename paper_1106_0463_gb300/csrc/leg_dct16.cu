@@ -204,7 +204,10 @@ template <int LOG2H> struct D16 {
     // resident CTAs per SM the register allocation aims at: six for CTAs of
     // 128 threads (H <= 1024; 80 registers, measured 51 us against 53 us at
     // H = 512 for B = 4096), none imposed for larger CTAs
-    static constexpr int MINB = THREADS <= 128 ? 6 : 1;
+    // resident CTAs per SM asked of the register allocator: about 24-32 warps
+    // per SM (80 registers at 128 and 256 threads, 64 at 512; 158 and 128
+    // registers without the target left one CTA per SM)
+    static constexpr int MINB = THREADS <= 128 ? 6 : THREADS == 256 ? 3 : THREADS == 512 ? 2 : 1;
     static constexpr int SLOTS = H + H / E + 1;                     // padded complex slots per function
     static constexpr int WARPS = T / 32;
     // FFT buffer: one padding slot per E complex values; real view (X): one
