@@ -410,7 +410,7 @@ def gpu_arm(args, rank, world, local_rank):
     e2e = {"value": whole_job_rate(world, B * N, e2e_step), "unit": UNIT,
            "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
            "d2h_bytes_per_step": c_host.numel() * c_host.element_size(),
-           "api": "leg_forward_host (pinned host buffers, copies overlapped with the kernels)",
+           "api": "leg_forward_host (pinned host buffers, read and written in place by the kernels)",
            "ms_per_step": e2e_step, "bare_copy_ms": copy_ms}
 
     if rank != 0:

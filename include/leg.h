@@ -311,9 +311,15 @@ LEG_API int leg_forward_noalloc(leg_plan_t plan, const float *f, float *c, int B
  * computation.  (A library convenience with no counterpart in the paper.)
  *   f_host  host, B x K (FP64 for LEG_F64, FP32 otherwise), row-major;
  *   c_host  host, B x N (same type); overwritten.
- * For LEG_SPLIT_FP16 plans the input goes over in four pieces on an internal
- * stream and the split of each piece starts when it has landed; the
- * coefficients come back per piece while the next piece is transformed.
+ * For LEG_SPLIT_FP16 and LEG_BF16 plans, page-locked host buffers that are
+ * mapped into the device's address space (cudaHostAlloc, cudaHostRegister
+ * with cudaHostRegisterMapped, pinned tensors on unified-addressing systems)
+ * are read and written in place by the kernels: the input split reads each
+ * row of f once over the host link and the last kernel writes each
+ * coefficient once, with no staging copy.
+ * Otherwise, for LEG_SPLIT_FP16 plans the input goes over in four pieces on
+ * an internal stream and the split of each piece starts when it has landed;
+ * the coefficients come back per piece while the next piece is transformed.
  * Results equal leg_forward's bit for bit.  Ordered after the work already on
  * `stream`; c_host is complete once `stream` has reached the end of the call
  * (synchronise `stream` before reading it); both host buffers must stay valid

@@ -1,4 +1,7 @@
-// leg_forward_host: leg_forward on host buffers.  The batch is copied to the
+// leg_forward_host: leg_forward on host buffers.  Page-locked host buffers
+// mapped into the device's address space are used in place by the split-FP16
+// and BF16 paths (their first kernel reads each input value once, their last
+// writes each coefficient once).  Otherwise the batch is copied to the
 // device, transformed and copied back with the copies overlapped with the
 // computation: for the split-FP16 path the host-to-device copy runs in
 // LEG_HOST_CHUNKS pieces on an internal stream and the input split of each
@@ -69,6 +72,19 @@ int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
     return LEG_OK;
 }
 
+// The device address of host memory the GPU can access in place (page-locked
+// memory, mapped into the device's address space), or nullptr.
+const void *device_view(const void *host)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || !a.devicePointer) return nullptr;
+    return a.devicePointer;
+}
+
 }  // namespace
 
 extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, int B, cudaStream_t st)
@@ -83,6 +99,15 @@ extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, 
     const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
     int rc = leg_plan_reserve(p, B);
     if (rc) return rc;
+    // page-locked, mapped host buffers: the kernels read f and write c in
+    // place over the host link (the split reads each row once, the transform
+    // writes each coefficient once), so the transfers overlap the computation
+    // with no staging copy
+    if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16) {   // the SIMT GEMMs re-read f per tile
+        const void *fv = device_view(f_host);
+        void *cv = const_cast<void *>(device_view(c_host));
+        if (fv && cv) return leg_forward(p, fv, cv, B, st);
+    }
     LegHostState *h = nullptr;
     if ((rc = host_state(p, B, eb, &h))) return rc;
 

@@ -58,6 +58,21 @@ def test_forward_host_full_size_matches_oracle(leg, oracle):
     assert err < 1e-6
 
 
+def test_forward_host_registered_and_staged_paths_agree(leg):
+    """Pinned tensors are mapped host memory (read in place by the kernels);
+    pageable tensors go through the staged copies; both give leg_forward's
+    coefficients bit for bit, including for the collapsed plan."""
+    N, M, K, B = 128, 512, 257, 777
+    for flags in (0, 2):
+        plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16, flags=flags)
+        f = inputs(B, K, 9)
+        ref = plan.forward(f.cuda()).cpu()
+        pinned = plan.forward_host(f.pin_memory(), torch.empty((B, N)).pin_memory())
+        staged = plan.forward_host(f.clone(), torch.empty((B, N)))
+        assert torch.equal(pinned, ref) and torch.equal(staged, ref)
+        plan.status()
+
+
 def test_forward_host_rejects_device_tensors(leg):
     plan = leg.Plan(16, 64, 17, 0, leg.SPLIT_FP16)
     with pytest.raises(ValueError):
