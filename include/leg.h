@@ -146,6 +146,13 @@ LEG_API int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *
  *   B  >= 0; B = 0 is a no-op.
  * Enqueued on stream; f and c must not overlap.  Concurrent calls on one
  * plan from different streams race on its workspace: use one plan per stream.
+ * The kernels are chained by programmatic dependent launch.  The first call
+ * with given (f, c, B) and launch settings runs its launches directly, the
+ * second captures them into a CUDA graph (on a stream of the plan's own) and
+ * later ones replay that graph on `stream`; a change of f, c, B, the
+ * workspace, the tile width, the transform kernel or the wait limit starts
+ * over.  A call made while `stream` is being captured by the caller launches
+ * directly, so its kernels become part of the caller's graph.
  */
 LEG_API int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream);
 
