@@ -104,3 +104,24 @@ def test_degenerate_inputs(leg, oracle):
     assert abs(c[1, 0] - 3.25) < 1e-6 * 3.25 and np.max(np.abs(c[1, 1:])) < 1e-6 * 3.25
     ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f[2:].astype(np.float64))
     assert relerr(c[2:], ref) < 1e-6
+
+
+@pytest.mark.parametrize("N,M,K,B", [(512, 2048, 2049, 600), (2048, 8192, 1025, 160), (256, 1024, 4097, 1000)])
+def test_partial_wave_shapes_match_oracle(leg, oracle, N, M, K, B):
+    """Shapes whose GEMM tiles leave the last wave of CTA pairs partly empty
+    (and a ragged last function tile): the forward against the oracle, and
+    the backward GEMM through <L f, v> = <f, L^T v>."""
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    f = cheb_inputs(B, K, seed=B)
+    c = plan.forward(torch.from_numpy(f).cuda())
+    plan.status()
+    sample = np.random.default_rng(B).choice(B, 6, replace=False)
+    ref = oracle.coeffs_abel(N, M, plan.Q, f_cl=f[sample].astype(np.float64))
+    assert relerr(c.double().cpu().numpy()[sample], ref) < 1e-6
+    v = np.random.default_rng(1).standard_normal((B, N)).astype(np.float32)
+    df = plan.backward(torch.from_numpy(v).cuda())
+    plan.status()
+    lhs = np.sum(c.double().cpu().numpy() * v.astype(np.float64), axis=1)      # <L f, v> per function
+    rhs = np.sum(f.astype(np.float64) * df.double().cpu().numpy(), axis=1)     # <f, L^T v>
+    scale = np.sqrt(np.sum(c.double().cpu().numpy() ** 2, 1) * np.sum(v.astype(np.float64) ** 2, 1))
+    assert np.max(np.abs(lhs - rhs) / scale) < 2e-6
