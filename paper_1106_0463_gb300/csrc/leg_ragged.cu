@@ -4,9 +4,11 @@
 //   2. ONE persistent tcgen05 launch over the tiles of every bucket's Abel GEMM
 //      (the problems are ordered by K-depth; CTA c takes tiles c, c + #SMs, ...),
 //   3. one transform launch per bucket, scattering each function's first n_out
-//      coefficients into the packed output,
-// the whole sequence captured once in a CUDA graph on a private stream and
-// replayed on later calls.  Method: arXiv:1106.0463, Theorem 1 (Eq. 2.4,
+//      coefficients into the packed output; the buckets read disjoint G
+//      buffers and write disjoint output ranges, so their launches run
+//      concurrently on LEG_RAGGED_LANES streams (the largest bucket first),
+// the whole sequence captured once in a CUDA graph on a private stream (the
+// lanes become parallel branches) and replayed on later calls.  Method: arXiv:1106.0463, Theorem 1 (Eq. 2.4,
 // Eq. 2.5), per bucket exactly as leg_forward.
 //
 // Also: leg_sample_cl, the on-device closed-form sampler used to generate
@@ -20,6 +22,10 @@
 #include <vector>
 
 #include "leg_internal.cuh"
+
+// streams the per-bucket transforms are spread over (the private stream and
+// LEG_RAGGED_LANES - 1 more)
+constexpr int LEG_RAGGED_LANES = 4;
 
 struct leg_ragged {
     int device = 0, nplans = 0, count = 0;
@@ -39,6 +45,9 @@ struct leg_ragged {
     long long wait_limit = 2000000000LL;
     cudaStream_t rs = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    cudaStream_t lane[LEG_RAGGED_LANES - 1] = {};
+    cudaEvent_t ev_gemm = nullptr, ev_lane[LEG_RAGGED_LANES - 1] = {};
+    std::vector<int> fft_order;   // buckets by transform work, largest first
     cudaGraphExec_t gexec = nullptr;
     const void *g_f = nullptr;
     void *g_c = nullptr;
@@ -53,6 +62,11 @@ void free_ragged(leg_ragged *r)
     if (r->gexec) cudaGraphExecDestroy(r->gexec);
     if (r->ev_in) cudaEventDestroy(r->ev_in);
     if (r->ev_out) cudaEventDestroy(r->ev_out);
+    if (r->ev_gemm) cudaEventDestroy(r->ev_gemm);
+    for (int i = 0; i < LEG_RAGGED_LANES - 1; ++i) {
+        if (r->ev_lane[i]) cudaEventDestroy(r->ev_lane[i]);
+        if (r->lane[i]) cudaStreamDestroy(r->lane[i]);
+    }
     if (r->rs) cudaStreamDestroy(r->rs);
     cudaFree(r->d_bucket);
     cudaFree(r->d_row);
@@ -82,11 +96,24 @@ int enqueue(leg_ragged *r, const float *f, float *c, cudaStream_t st)
     int rc = leg_split_ragged(f, r->d_in_off, r->d_bucket, r->d_row, r->d_bk, r->count, r->max_k, st);
     if (rc) return rc;
     if ((rc = leg_gemm_split_grouped(r->d_probs, r->nprob, r->ntiles, r->tn, r->status, r->wait_limit, st))) return rc;
-    for (int p = 0; p < r->nplans; ++p) {
-        if (r->Bp[p] == 0) continue;
+    // bucket i of fft_order goes to lane i mod LEG_RAGGED_LANES (lane 0 = st):
+    // the largest transforms start first, one per lane, and the small ones
+    // fill the GPU beside them
+    const int nb = (int)r->fft_order.size();
+    const int nl = nb < LEG_RAGGED_LANES ? nb : LEG_RAGGED_LANES;
+    if (nl > 1) {
+        LEG_CUDA_TRY(cudaEventRecord(r->ev_gemm, st));
+        for (int l = 1; l < nl; ++l) LEG_CUDA_TRY(cudaStreamWaitEvent(r->lane[l - 1], r->ev_gemm, 0));
+    }
+    for (int i = 0; i < nb; ++i) {
+        const int p = r->fft_order[i], l = i % LEG_RAGGED_LANES;
         rc = leg_fft_forward_ragged(r->plans[p], r->G[p], r->ldg[p], c, r->Bp[p], r->d_rowfn[p], r->d_out_off,
-                                    r->d_n_out, st);
+                                    r->d_n_out, l ? r->lane[l - 1] : st);
         if (rc) return rc;
+    }
+    for (int l = 1; l < nl; ++l) {
+        LEG_CUDA_TRY(cudaEventRecord(r->ev_lane[l - 1], r->lane[l - 1]));
+        LEG_CUDA_TRY(cudaStreamWaitEvent(st, r->ev_lane[l - 1], 0));
     }
     return LEG_OK;
 }
@@ -262,8 +289,18 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         return fail(leg_set_error(LEG_ERR_OOM, "status allocation failed"));
     if (cudaStreamCreateWithFlags(&r->rs, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&r->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess)
+        cudaEventCreateWithFlags(&r->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&r->ev_gemm, cudaEventDisableTiming) != cudaSuccess)
         return fail(leg_set_error(LEG_ERR_CUDA, "stream/event creation failed"));
+    for (int i = 0; i < LEG_RAGGED_LANES - 1; ++i)
+        if (cudaStreamCreateWithFlags(&r->lane[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&r->ev_lane[i], cudaEventDisableTiming) != cudaSuccess)
+            return fail(leg_set_error(LEG_ERR_CUDA, "stream/event creation failed"));
+    // transform work of a bucket ~ functions x M log M
+    for (int p = 0; p < nplans; ++p)
+        if (r->Bp[p] > 0) r->fft_order.push_back(p);
+    auto work = [&](int p) { return (double)r->Bp[p] * r->plans[p]->M * std::log2((double)r->plans[p]->M); };
+    std::stable_sort(r->fft_order.begin(), r->fft_order.end(), [&](int a, int b) { return work(a) > work(b); });
     if (cudaDeviceSynchronize() != cudaSuccess) return fail(leg_set_error(LEG_ERR_CUDA, "synchronise failed"));
     *out = r;
     return LEG_OK;
