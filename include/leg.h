@@ -64,7 +64,8 @@ extern "C" {
  *                  FP32 accumulation (tcgen05), FP32 FFT.
  *   LEG_SPLIT_FP16 f, c in FP32; operator split into three FP16 slices (a
  *                  fixed-point leading slice, two residual slices), input
- *                  into seven pre-scaled FP16 planes; eight tcgen05 products
+ *                  into seven pre-scaled FP16 planes (slice widths chosen by
+ *                  K: 15 + 8 bits for K <= 1025, 16 + 7 above); eight tcgen05 products
  *                  into three FP32 TMEM accumulators of which the leading one
  *                  is exact, combined into a double-float result;
  *                  double-float FFT.  The path aimed at a 1e-6 relative error.

@@ -127,6 +127,7 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
     p->N = N;
     p->M = M;
     p->K = K;
+    p->fbits = leg_split_fbits(K);
     p->Q = (Q == 0) ? (K + 1) / 2 : Q;
     p->dtype = dtype;
     p->flags = flags;
@@ -171,6 +172,7 @@ extern "C" int leg_plan_create_like(leg_plan_t *out, leg_plan_t src, int dtype)
     p->N = src->N;
     p->M = src->M;
     p->K = src->K;
+    p->fbits = src->fbits;
     p->Q = src->Q;
     p->dtype = dtype;
     p->flags = src->flags;

@@ -10,10 +10,11 @@
 //
 // LEG_SPLIT_FP16 (three-slice split, eight products, three accumulators):
 //   each operand row is scaled by a power of two (the operator by its L1
-//   norm, the input by its max-norm) and split into FP16 slices,
-//   s = LEG_SPLIT_FBITS = 7, LEG_SPLIT_ABITS = 16:
-//     a = A0 + 2^-s A1 + 2^-2s A2s,     A0 on a 2^-16 grid,
-//     f = F0 + 2^-s r,  r = F1 + (r - F1),   F0 on a 2^-7 grid.
+//   norm, the input by its max-norm) and split into FP16 slices, with the
+//   plan's slice width s (8 for K <= 1025, else 7; leg_split_fbits) and
+//   abits = 23 - s:
+//     a = A0 + 2^-s A1 + 2^-2s A2s,     A0 on a 2^-abits grid,
+//     f = F0 + 2^-s r,  r = F1 + (r - F1),   F0 on a 2^-s grid.
 //   acc0 takes A0 F0 over the whole tile: the products lie on a 2^-23 grid
 //   and every partial sum stays below 2, so it is EXACT in FP32 whatever the
 //   order or truncation of the tensor core's additions.
@@ -362,7 +363,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         const uint32_t acc_empty0 = sm100::mapa_shared(sm100::smem_u32(&acc_empty), 0u);
         const int nunits = tn >> 4;
         constexpr int MU = max_tn<NPROD>() / 64;        // units per warp, at most
-        constexpr float W1 = 1.0f / (float)(1 << LEG_SPLIT_FBITS);
         uint32_t cc = 0;
         int ti = 0;
         bool ok = true;
@@ -455,10 +455,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     if constexpr (NPROD == 1) {
                         static_cast<float *>(pr.out)[o] = a0[16 * m + i];
                     } else if constexpr (OUT_DF) {
-                        const dfl sm = df_two_sum(a0[16 * m + i], r1[16 * m + i] * W1);
+                        const dfl sm = df_two_sum(a0[16 * m + i], r1[16 * m + i] * pr.w1);
                         static_cast<float2 *>(pr.out)[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
                     } else {
-                        static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], W1, a0[16 * m + i]), e);
+                        static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], pr.w1, a0[16 * m + i]), e);
                     }
                 }
             }
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
 }
 
 // ---------------------------------------------------------------- input split
-// One CTA per row: power-of-two scale 2^e >= max|x|, then with s = LEG_SPLIT_FBITS
+// One CTA per row: power-of-two scale 2^e >= max|x|, then with s = in.fbits
 //   xs = x 2^-e,  F0 = round(xs 2^s) 2^-s,  r = (xs - F0) 2^s,  F1 = fp16(r),
 // and the seven planes  F0, F1, fp16(r - F1), fp16(2^-s F1), 2^-s F0,
 // fp16(2^-2s F1), fp16(2^-s (r - F1))  (plane p at P + p * pstride), so that
@@ -520,10 +520,11 @@ template <> __device__ __forceinline__ float zero_of<float>() { return 0.0f; }
 template <> __device__ __forceinline__ float2 zero_of<float2>() { return make_float2(0.0f, 0.0f); }
 
 // Planes of two scaled values (h, l: leading and trailing parts of x 2^-e)
-// as FP16 pairs: the seven planes' values for elements i and i + 1.
-__device__ __forceinline__ void split_pair(float ha, float la, float hb, float lb, __half2 (&o)[LEG_SPLIT_NF])
+// as FP16 pairs: the seven planes' values for elements i and i + 1
+// (SC = 2^s, ISC = 2^-s).
+__device__ __forceinline__ void split_pair(float ha, float la, float hb, float lb, float SC, float ISC,
+                                           __half2 (&o)[LEG_SPLIT_NF])
 {
-    constexpr float SC = (float)(1 << LEG_SPLIT_FBITS), ISC = 1.0f / SC;
     const float x0a = rintf(ha * SC) * ISC, x0b = rintf(hb * SC) * ISC;
     const float ra = (ha - x0a) * SC + la * SC, rb = (hb - x0b) * SC + lb * SC;
     const __half2 f1 = __floats2half2_rn(ra, rb);
@@ -540,8 +541,9 @@ __device__ __forceinline__ void split_pair(float ha, float la, float hb, float l
 
 template <class T, bool STAGE>
 __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
-                                          size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00)
+                                          size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00, int fbits)
 {
+    const float SC = __int_as_float((127 + fbits) << 23), ISC = __int_as_float((127 - fbits) << 23);
     __shared__ float red[SPLIT_THREADS / 32];
     __shared__ int s_e;
     extern __shared__ __align__(16) unsigned char split_smem[];
@@ -605,7 +607,7 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             __half2 q[LEG_SPLIT_NF];
-            split_pair(h[2 * i], l[2 * i], h[2 * i + 1], l[2 * i + 1], q);
+            split_pair(h[2 * i], l[2 * i], h[2 * i + 1], l[2 * i + 1], SC, ISC, q);
 #pragma unroll
             for (int p = 0; p < LEG_SPLIT_NF; ++p) o[p][i] = q[p];
         }
@@ -621,7 +623,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__re
 {
     const int b = blockIdx.x;
     split_row<T, STAGE>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
-                        G ? G + (size_t)b * ldg : nullptr, a00);
+                        G ? G + (size_t)b * ldg : nullptr, a00, in.fbits);
     leg_griddep_trigger();   // after this CTA's stores: the GEMM's setup may start
 }
 
@@ -638,7 +640,7 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float
     const LegRaggedBucket &b = bk[bucket[i]];
     const int r = row[i];
     split_row<float, STAGE>(f_packed + in_off[i], b.K, b.Kp, b.in.base + (size_t)r * b.in.ld, b.in.pstride,
-                           b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00);
+                           b.in.fexp + r, b.G + (size_t)r * b.ldg, b.a00, b.in.fbits);
     leg_griddep_trigger();
 }
 
@@ -674,8 +676,10 @@ __global__ void __launch_bounds__(256) bf16_rows_kernel(const float *__restrict_
 // 2^e_k >= sum_j |A[j,k]|, split as the operator's own planes.
 __global__ void __launch_bounds__(256) split_cols_kernel(const double *__restrict__ A, int rows, int K, int npr,
                                                          __half *__restrict__ T0, __half *__restrict__ T1,
-                                                         __half *__restrict__ T2, int *__restrict__ colexp)
+                                                         __half *__restrict__ T2, int *__restrict__ colexp,
+                                                         int fbits)
 {
+    const int abits = LEG_SPLIT_GRID - fbits;
     const int k = blockIdx.x;
     __shared__ double red[8];
     __shared__ double s_inv;
@@ -700,14 +704,14 @@ __global__ void __launch_bounds__(256) split_cols_kernel(const double *__restric
     for (int j = threadIdx.x; j < npr; j += blockDim.x) {
         double a = (j < rows) ? A[(size_t)j * K + k] * inv : 0.0;
         double a0;
-        if (fabs(a) >= ldexp(1.0, 10 - LEG_SPLIT_ABITS)) a0 = (double)__double2half(a);
-        else a0 = rint(ldexp(a, LEG_SPLIT_ABITS)) * ldexp(1.0, -LEG_SPLIT_ABITS);
-        double r1 = ldexp(a - a0, LEG_SPLIT_FBITS);
+        if (fabs(a) >= ldexp(1.0, 10 - abits)) a0 = (double)__double2half(a);
+        else a0 = rint(ldexp(a, abits)) * ldexp(1.0, -abits);
+        double r1 = ldexp(a - a0, fbits);
         __half h1 = __double2half(r1);
         size_t o = (size_t)k * npr + j;
         T0[o] = __double2half(a0);
         T1[o] = h1;
-        T2[o] = __double2half(ldexp(r1 - (double)h1, LEG_SPLIT_FBITS));
+        T2[o] = __double2half(ldexp(r1 - (double)h1, fbits));
     }
 }
 
@@ -876,6 +880,7 @@ void finish_problem(TcProblem *pr, const int *aexp, const int *fexp, void *out, 
     pr->ntm = ceil_div(rows, PAIR_M);
     pr->ntn = ceil_div(B, tn);
     pr->tile0 = 0;
+    pr->w1 = 1.0f;
 }
 
 // Split problem: operator planes a0 + s apstride (rows x Kc, row stride lda),
@@ -887,6 +892,7 @@ int make_split(TcProblem *pr, const __half *a0, size_t apstride, int rows, int l
     if ((rc = make_map(&pr->a, a0, Kc, rows, lda, LEG_SPLIT_NA, apstride, false, CTA_M))) return rc;
     if ((rc = make_map(&pr->f, in.base, Kc, B, in.ld, LEG_SPLIT_NF, in.pstride, false, tn / 2))) return rc;
     finish_problem(pr, aexp, in.fexp, out, ldo, rows, B, Kc, tn);
+    pr->w1 = ldexpf(1.0f, -in.fbits);
     return LEG_OK;
 }
 
@@ -901,6 +907,7 @@ LegSplitIn leg_split_workspace(const leg_plan *p)
     in.pstride = (size_t)p->ws_B * p->ldf;
     in.ld = p->ldf;
     in.fexp = p->fexp;
+    in.fbits = p->fbits;
     return in;
 }
 
@@ -927,7 +934,7 @@ int leg_build_split_transposed(leg_plan *p)
     p->AhT[2] = p->AhT[0] + 2 * plane;
     LEG_CUDA_TRY(cudaMalloc(&p->colexp, sizeof(int) * p->K));
     split_cols_kernel<<<p->K, 256>>>(p->collapsed() ? p->L64 : p->A64, p->grows, p->K, npr, p->AhT[0], p->AhT[1],
-                                     p->AhT[2], p->colexp);
+                                     p->AhT[2], p->colexp, p->fbits);
     LEG_LAUNCH_CHECK("split_cols_kernel");
     return LEG_OK;
 }

@@ -55,16 +55,18 @@ constexpr int LEG_MAX_M = 32768;
 constexpr int LEG_MAX_K = 16385;
 
 // Split-FP16 scheme (fixed-point leading slice): granularity exponents of the
-// leading slices of the operator (A0 on a 2^-LEG_SPLIT_ABITS grid) and of the
-// input (F0 on a 2^-LEG_SPLIT_FBITS grid).  Their sum is 23, so products
+// leading slices of the operator (A0 on a 2^-abits grid) and of the input (F0
+// on a 2^-s grid, s = fbits).  Their sum is LEG_SPLIT_GRID = 23, so products
 // A0*F0 lie on a 2^-23 grid and every partial sum (below 2 in magnitude for
 // L1-normalised operator rows) is exact in FP32.  The residual slices carry
-// weights 2^-s and 2^-2s, s = LEG_SPLIT_FBITS.  A finer A0 grid (16 bits)
-// keeps the entries of long operator rows (|a| ~ 1/K) mostly in A0: with
-// (14, 9) the K = 8193 sweep measured 1.3e-6 against 3e-7 here.
-constexpr int LEG_SPLIT_ABITS = 16;
-constexpr int LEG_SPLIT_FBITS = 7;
-static_assert(LEG_SPLIT_ABITS + LEG_SPLIT_FBITS == 23, "accumulator 0 exactness");
+// weights 2^-s and 2^-2s.  The split is chosen per plan by K: operator
+// entries are ~1/K, so long rows need a fine A0 grid (abits 16: with (15, 8)
+// the K = 8193 workload measured 1.0e-6 against 2.8e-7, with (14, 9) 1.3e-6),
+// while for K <= 1025 a finer F0 grid wins (8 bits: a peaked input such as
+// (1 - 2xt + t^2)^-1/2, t = 0.95, keeps more of itself in F0, and the error
+// of the N = 8192 ragged bucket fell from 7.5e-7 to 4.1e-7).
+constexpr int LEG_SPLIT_GRID = 23;
+__host__ __device__ inline int leg_split_fbits(int K) { return K <= 1025 ? 8 : 7; }
 // Planes of the split-FP16 GEMM: the operator side keeps its three slices
 // A0, A1, A2s; the input side carries F0, F1, the residual r - F1 at weight
 // 2^-s, and the pre-scaled copies 2^-s F1, 2^-s F0, 2^-2s F1, 2^-s (r - F1),
@@ -81,6 +83,7 @@ constexpr int LEG_HOST_CHUNKS = 4;     // pieces of a leg_forward_host batch (sp
 
 struct leg_plan {
     int N, M, K, Q, dtype;
+    int fbits;  // split-FP16 slice width s (leg_split_fbits(K)); the operator's is LEG_SPLIT_GRID - s
     unsigned flags;
     int L;      // M/2: length of the complex FFT (real transform of length M)
     int rows;   // M/2 + 1 distinct rows of the Abel operator (Eq. 2.12)
@@ -162,6 +165,7 @@ struct LegSplitIn {
     size_t pstride;   // elements between consecutive planes
     int ld;           // row stride (elements), a multiple of LEG_KPAD
     int *fexp;        // per-row power-of-two scales
+    int fbits;        // slice width s of the split (the plan's)
 };
 
 // One GEMM problem of the tcgen05 kernel (leg_gemm_tc.cu):
@@ -179,6 +183,7 @@ struct TcProblem {
     int tn;                  // functions per pair tile (multiple of 16, <= 256)
     int ntm, ntn;            // tiles along rows (256 each) and along functions (tn each)
     int tile0;               // first global tile index of this problem (grouped launches)
+    float w1;                // 2^-s: weight of acc1 and acc2 (split path)
 };
 
 // Device descriptor of one bucket of a ragged batch (input-split targets).

@@ -94,6 +94,7 @@ extern "C" int leg_forward_noalloc(leg_plan_t p, const float *f, float *c, int B
     in.pstride = plane / sizeof(__half);
     in.ld = p->Kp;
     in.fexp = reinterpret_cast<int *>(base + LEG_SPLIT_NF * plane);
+    in.fbits = p->fbits;
     float2 *G = reinterpret_cast<float2 *>(base + LEG_SPLIT_NF * plane + exps);
 
     if ((rc = leg_split_prepare_input_into(p, f, B, in, G, ldg, st))) return rc;

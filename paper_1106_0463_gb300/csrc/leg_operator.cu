@@ -168,14 +168,16 @@ __global__ void plane_bf16_kernel(const double *A, int K, int Kp, __nv_bfloat16 
 }
 
 // Split-FP16 planes of row j.  Row scale 2^e_j >= sum_k |A[j,k]| (so the
-// scaled row has L1 norm <= 1).  With a = A[j,k] / 2^e_j, s = LEG_SPLIT_FBITS:
-//   A0 = a rounded to FP16 but never finer than 2^-LEG_SPLIT_ABITS (a
-//        fixed-point grid for small |a|, ordinary FP16 rounding above),
+// scaled row has L1 norm <= 1).  With a = A[j,k] / 2^e_j, s = fbits and
+// abits = LEG_SPLIT_GRID - s:
+//   A0 = a rounded to FP16 but never finer than 2^-abits (a fixed-point
+//        grid for small |a|, ordinary FP16 rounding above),
 //   r1 = (a - A0) 2^s,  A1 = fp16(r1),  A2s = fp16((r1 - A1) 2^s),
 // so a = A0 + 2^-s A1 + 2^-2s A2s up to the FP16 rounding of A2s.
 __global__ void plane_split_kernel(const double *A, int K, int Kp, __half *A0p, __half *A1p,
-                                   __half *A2p, int *rowexp)
+                                   __half *A2p, int *rowexp, int fbits)
 {
+    const int abits = LEG_SPLIT_GRID - fbits;
     const int j = blockIdx.x;
     __shared__ double red[32];
     double s = 0.0;
@@ -201,11 +203,11 @@ __global__ void plane_split_kernel(const double *A, int K, int Kp, __half *A0p, 
     for (int k = threadIdx.x; k < Kp; k += blockDim.x) {
         double a = (k < K) ? A[(size_t)j * K + k] * inv : 0.0;
         double a0;
-        if (fabs(a) >= ldexp(1.0, 10 - LEG_SPLIT_ABITS)) a0 = (double)__double2half(a);   // FP16 ulp >= grid
-        else a0 = rint(ldexp(a, LEG_SPLIT_ABITS)) * ldexp(1.0, -LEG_SPLIT_ABITS);
-        double r1 = ldexp(a - a0, LEG_SPLIT_FBITS);
+        if (fabs(a) >= ldexp(1.0, 10 - abits)) a0 = (double)__double2half(a);   // FP16 ulp >= grid
+        else a0 = rint(ldexp(a, abits)) * ldexp(1.0, -abits);
+        double r1 = ldexp(a - a0, fbits);
         __half h1 = __double2half(r1);
-        __half h2 = __double2half(ldexp(r1 - (double)h1, LEG_SPLIT_FBITS));
+        __half h2 = __double2half(ldexp(r1 - (double)h1, fbits));
         size_t o = (size_t)j * Kp + k;
         A0p[o] = __double2half(a0);
         A1p[o] = h1;
@@ -376,7 +378,7 @@ int leg_build_planes(leg_plan *p)
         p->Ah[1] = p->Ah[0] + plane;
         p->Ah[2] = p->Ah[0] + 2 * plane;
         LEG_TRY_CLEAN(cudaMalloc(&p->rowexp, sizeof(int) * rows));
-        plane_split_kernel<<<rows, 256>>>(S, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp);
+        plane_split_kernel<<<rows, 256>>>(S, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp, p->fbits);
         LEG_TRY_CLEAN(cudaGetLastError());
         int rc2 = leg_build_split_transposed(p);
         if (rc2) {

@@ -259,6 +259,7 @@ extern "C" int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int
         bk[p].in.pstride = Bz * pl->Kp;
         bk[p].in.ld = pl->Kp;
         bk[p].in.fexp = r->fexp[p];
+        bk[p].in.fbits = pl->fbits;
         bk[p].G = r->G[p];
         bk[p].ldg = r->ldg[p];
         const float ah = (float)pl->a00;
