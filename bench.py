@@ -196,8 +196,8 @@ ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
 # (one ncu capture per kernel); keyed by (stage, path, workload).
 TRAFFIC = {
-    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 72888576,   # tc_gemm_pair_split_fp16_...
-    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34175744,         # dct16_forward_dfl_...
+    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 69294080,   # tc_gemm_pair_split_fp16_...
+    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34181120,         # dct16_forward_dfl_...
 }
 
 
