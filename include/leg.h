@@ -202,16 +202,19 @@ LEG_API int leg_plain_forward(leg_plan_t plan, int family, const double *params,
  *   in_off[i]    offset (in floats) of its K samples in the packed input;
  *   out_off[i]   offset (in floats) of its n_out[i] coefficients in the
  *                packed output.
- * Allocates the per-bucket workspaces and a private stream; synchronises.
+ * Allocates the per-bucket workspaces, a private stream and three streams
+ * for the concurrent transforms; synchronises.
  * The plans must outlive the batch.
  *
  * leg_forward_ragged -- Theorem 1 (Eq. 2.4, Eq. 2.5) for every function of
  * the batch: one input-split launch over all functions, ONE persistent
  * tcgen05 launch over the Abel-GEMM tiles of all buckets, one transform
- * launch per bucket writing the packed output.  The first call runs the
+ * launch per bucket writing the packed output (the transforms of the buckets
+ * run concurrently on the batch's internal streams).  The first call runs the
  * sequence directly; later calls replay it as a CUDA graph (captured again
- * when f_packed or c_packed change).  Ordered after prior work on `stream`,
- * and later work on `stream` waits for it.  Device pointers.
+ * when f_packed or c_packed change).  When `stream` is itself being captured,
+ * the launches join the caller's graph instead.  Ordered after prior work on
+ * `stream`, and later work on `stream` waits for it.  Device pointers.
  *
  * leg_ragged_status -- as leg_plan_status, for the batch's kernels.
  */

@@ -315,6 +315,10 @@ extern "C" int leg_forward_ragged(leg_ragged_t r, const float *f_packed, float *
     int dev = -1;
     LEG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev != r->device) return leg_set_error(LEG_ERR_INVALID_ARG, "current device differs from the batch's");
+    // the caller is capturing its own graph: the launches join it directly
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return enqueue(r, f_packed, c_packed, st);
     LEG_CUDA_TRY(cudaEventRecord(r->ev_in, st));
     LEG_CUDA_TRY(cudaStreamWaitEvent(r->rs, r->ev_in, 0));
     int rc = LEG_OK;

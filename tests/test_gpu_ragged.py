@@ -87,3 +87,25 @@ def test_ragged_small(leg, oracle):
 def test_ragged_10000(leg, oracle):
     cfg = workloads.CONFIGS["ragged_10000"]
     check(leg, oracle, cfg["count"], cfg["Nmin"], cfg["Nmax"], workloads.SEED_BASE + 3, per_bucket=1)
+
+
+def test_ragged_inside_a_caller_capture(leg):
+    """Called while the caller's stream is capturing, the batch's launches
+    (the transforms on their parallel branches included) join the caller's
+    graph; replaying it gives the direct launches' coefficients bit for bit."""
+    fam, par, n, lay, plans, batch, f = build(leg, 200, 32, 2048, 23)
+    ref = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
+    batch.forward(f, ref)
+    torch.cuda.synchronize()
+    c = torch.full((lay["n_out"],), float("nan"), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            batch.forward(f, c)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    torch.cuda.synchronize()
+    batch.status()
+    assert torch.equal(c, ref)
