@@ -46,7 +46,7 @@ UNIT = "coeffs/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="cheb_b4096_k1025_n512_m2048")
@@ -84,9 +84,19 @@ class ClockSampler:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+                 "-lms", "20"], stdout=self.fh, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+
+    def wait_first(self, timeout: float = 3.0):
+        """Block until the sampler has written its first sample (so that the
+        samples cover the work that follows), at most `timeout` seconds."""
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < timeout:
+            self.fh.flush()
+            if os.path.getsize(self.path) > 0:
+                return
+            time.sleep(0.01)
 
     def stop(self):
         if self.proc is None:
@@ -152,10 +162,11 @@ def reference_arm(args, rank, world):
     N, M, K = cfg["N"], cfg["M"], cfg["K"]
     Q = O.exact_tau_points(K)
     f = workloads.workload_inputs(name).astype(np.float64)
-    # size one step to about 2 s of CPU work
+    # size one step to about 2 s of CPU work, and all steps to about a minute
     base, n, dt = oracle_rate(name, seconds=6.0, max_fns=64)
     per_fn = dt / n
-    S = max(1, min(cfg["B"], int(2.0 / max(per_fn, 1e-9))))
+    budget = min(2.0, 60.0 / max(1, args.steps + args.warmup))
+    S = max(1, min(cfg["B"], int(budget / max(per_fn, 1e-9))))
     for _ in range(args.warmup):
         O.coeffs_abel(N, M, Q, f_cl=f[:S])
     times = []
@@ -220,7 +231,7 @@ def relerr(c, ref):
     return float(np.max(np.max(np.abs(c - ref), 1) / np.max(np.abs(ref), 1)))
 
 
-def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, flags=0):
+def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, flags=0, clocks=None):
     cfg = workloads.CONFIGS[name]
     B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
     dt = PATHS[path]
@@ -237,7 +248,11 @@ def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, f
         plan.forward(f, c)
     torch.cuda.synchronize()
     # timed steps: one event pair around the whole forward (kernels overlap
-    # through programmatic dependent launch), L2 flushed before each
+    # through programmatic dependent launch), L2 flushed before each; the
+    # clock sampler runs over exactly these steps
+    if clocks is not None:
+        clocks.start()
+        clocks.wait_first()
     step_ms = []
     for _ in range(steps):
         flush.zero_()
@@ -247,13 +262,15 @@ def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, f
         e1.record()
         e1.synchronize()
         step_ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop() if clocks is not None else None
     # stage breakdown: events between the kernels (serialises them), separate passes
     stage = []
     for _ in range(min(steps, 10)):
         flush.zero_()
         stage.append(plan.forward_profiled(f, c))
     plan.status()
-    out = {"plan": plan, "f": f, "c": c, "f_np": f_np, "plan_s": plan_s, "stage": stage, "step_ms": step_ms}
+    out = {"plan": plan, "f": f, "c": c, "f_np": f_np, "plan_s": plan_s, "stage": stage, "step_ms": step_ms,
+           "clk": clk}
     if sample_err:
         out["c_sample"] = c[:sample_err].double().cpu().numpy()
     return out
@@ -366,10 +383,9 @@ def gpu_arm(args, rank, world, local_rank):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local_rank].strip() if vis else str(local_rank)
     clocks = ClockSampler(phys)
-    clocks.start()
-    res = run_path(leg, torch, name, args.path, rank, args.steps, args.warmup, flush, sample_err=16)
+    res = run_path(leg, torch, name, args.path, rank, args.steps, args.warmup, flush, sample_err=16, clocks=clocks)
     barrier()
-    clk = clocks.stop()
+    clk = res["clk"]
     stage = np.array(res["stage"])              # profiled passes x 3 (ms)
     total_ms = float(np.sum(res["step_ms"]))
     total_ms = max_over_ranks(torch, dist, total_ms, "cuda")
