@@ -142,7 +142,7 @@ __device__ __forceinline__ float scale2(float x, int e)
     return (e >= -126 && e <= 127) ? x * __int_as_float((e + 127) << 23) : ldexpf(x, e);
 }
 
-// Warp-uniform bounded wait: lane 0 polls, the verdict is broadcast.
+// Warp-uniform bounded wait: lane 0 polls, the outcome is broadcast.
 __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long long limit,
                                           const volatile int *abort_flag)
 {
