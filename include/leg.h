@@ -187,9 +187,21 @@ LEG_API int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaS
  */
 #define LEG_FAMILY_GENFN 0
 #define LEG_FAMILY_EXP   1
-#define LEG_FAMILY_CHEB  2   /* leg_sample_cl only: sum_m coef_m T_m(x) */
+#define LEG_FAMILY_CHEB  2   /* leg_sample_cl, leg_plain_forward_cheb: sum_m coef_m T_m(x) */
 LEG_API int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
                       double *c, cudaStream_t stream);
+
+/*
+ * leg_plain_forward_cheb -- the plain method for Chebyshev series
+ * f(x) = sum_{m < Kc} coef[b, m] T_m(x) (the third ragged family): f is
+ * evaluated at the quadrature points by Clenshaw's recurrence, then the
+ * quadrature and the FFT as in leg_plain_forward.  FP64; N, M, Q of the plan.
+ *   coef  device, B x Kc doubles, row-major; 1 <= Kc <= 16385.
+ *   c     device, B x N doubles.
+ * Invalid sizes or null pointers: LEG_ERR_INVALID_ARG.
+ */
+LEG_API int leg_plain_forward_cheb(leg_plan_t plan, const double *coef, int Kc, int B, double *c,
+                                   cudaStream_t stream);
 
 /*
  * Ragged batches (functions of different sizes, grouped in size buckets).

@@ -72,6 +72,7 @@ def _load():
         "leg_forward_noalloc": ([vp, vp, vp, i, vp], i),
         "leg_forward_host": ([vp, vp, vp, i, vp], i),
         "leg_plain_forward": ([vp, i, vp, i, vp, vp], i),
+        "leg_plain_forward_cheb": ([vp, vp, i, i, vp, vp], i),
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
@@ -288,6 +289,18 @@ class Plan:
             c = torch.empty((B, self.N), dtype=torch.float64, device=params.device)
         pc = _dev_tensor(c, torch.float64, (B, self.N), "c")
         _check(_lib.leg_plain_forward(self._h, family, pp, B, pc, _stream(stream)))
+        return c
+
+    def plain_forward_cheb(self, coef: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """Plain method for Chebyshev series sum_m coef[b, m] T_m(x) (leg_plain_forward_cheb); FP64."""
+        if coef.dim() != 2:
+            raise ValueError("coef must be B x Kc")
+        B, Kc = coef.shape
+        pk = _dev_tensor(coef, torch.float64, (B, Kc), "coef")
+        if c is None:
+            c = torch.empty((B, self.N), dtype=torch.float64, device=coef.device)
+        pc = _dev_tensor(c, torch.float64, (B, self.N), "c")
+        _check(_lib.leg_plain_forward_cheb(self._h, pk, Kc, B, pc, _stream(stream)))
         return c
 
 

@@ -425,6 +425,28 @@ extern "C" int leg_backward(leg_plan_t p, const void *dc, void *df, int B, cudaS
     }
 }
 
+// The plain method's FP64 G (B rows) filled by `fill`, then the FP64 transform.
+template <class Fill>
+int plain_run(leg_plan *p, int B, double *c, cudaStream_t st, Fill fill)
+{
+    int rc = ensure_workspace(p, B);
+    if (rc) return rc;
+    // the FP64 plain path needs 8-byte G elements: the plan's G when it has
+    // them, else a stream-ordered allocation
+    double *G = nullptr;
+    int ldg = leg_round_up(p->rows, 8);
+    if (g_elem_bytes(p->dtype) >= sizeof(double) && p->G) {
+        G = static_cast<double *>(p->G);
+        ldg = p->ldg;
+    } else {
+        LEG_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&G), sizeof(double) * (size_t)B * ldg, st));
+    }
+    rc = fill(G, ldg);
+    if (!rc) rc = leg_fft_forward_f64(p, G, ldg, c, B, st);
+    if (G != p->G) cudaFreeAsync(G, st);
+    return rc;
+}
+
 extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params, int B, double *c,
                                  cudaStream_t st)
 {
@@ -435,21 +457,19 @@ extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params,
     if (B < 0 || B > 65535) return leg_set_error(LEG_ERR_INVALID_ARG, "B must be in [0, 65535]");
     if (B == 0) return LEG_OK;
     if (!params || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null params or c");
-    if ((rc = ensure_workspace(p, B))) return rc;
-    // the FP64 plain path needs 8-byte G elements; every dtype's G has at least
-    // B x ldg x 4 bytes, so use the backward buffer pair as one FP64 array when needed
-    double *G = nullptr;
-    int ldg = leg_round_up(p->rows, 8);
-    if (g_elem_bytes(p->dtype) >= sizeof(double) && p->G) {
-        G = static_cast<double *>(p->G);
-        ldg = p->ldg;
-    } else {
-        LEG_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&G), sizeof(double) * (size_t)B * ldg, st));
-    }
-    rc = leg_plain_g(p, family, params, B, G, ldg, st);
-    if (!rc) rc = leg_fft_forward_f64(p, G, ldg, c, B, st);
-    if (G != p->G) cudaFreeAsync(G, st);
-    return rc;
+    return plain_run(p, B, c, st, [&](double *G, int ldg) { return leg_plain_g(p, family, params, B, G, ldg, st); });
+}
+
+extern "C" int leg_plain_forward_cheb(leg_plan_t p, const double *coef, int Kc, int B, double *c, cudaStream_t st)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (Kc < 1 || Kc > LEG_MAX_K)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "Kc must be in [1, " + std::to_string(LEG_MAX_K) + "]");
+    if (B < 0 || B > 65535) return leg_set_error(LEG_ERR_INVALID_ARG, "B must be in [0, 65535]");
+    if (B == 0) return LEG_OK;
+    if (!coef || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null coef or c");
+    return plain_run(p, B, c, st, [&](double *G, int ldg) { return leg_plain_g_cheb(p, coef, Kc, B, G, ldg, st); });
 }
 
 extern "C" int leg_plan_status(leg_plan_t p, int reset)

@@ -234,6 +234,7 @@ int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,
                 cudaStream_t st);
+int leg_plain_g_cheb(const leg_plan *p, const double *coef, int Kc, int B, double *G, int ldg, cudaStream_t st);
 
 // split-FP16 tensor-core path (leg_gemm_tc.cu)
 LegSplitIn leg_split_workspace(const leg_plan *p);

@@ -3,7 +3,8 @@
 // points themselves,
 //     g_j = sum_q w_q f(x_jq),   1 - x_jq = 2 sin^2(pi j / M) (1 - tau_q^2),
 // for the rows j = 0..M/2 of the grid y_j = 2 pi j / M, in FP64.  The result
-// feeds the same FFT stage as the sampled path.
+// feeds the same FFT stage as the sampled path.  Families: the generating
+// function (Eq. 2.2), e^{ax}, and Chebyshev series given by coefficients.
 #include "leg_internal.cuh"
 
 namespace {
@@ -34,7 +35,48 @@ __global__ void plain_g_kernel(int M, int Q, int family, const double *__restric
     G[(size_t)b * ldg + j] = acc;
 }
 
+// f(x) = sum_{m < Kc} coef[m] T_m(x) by Clenshaw's recurrence in FP64,
+//   b_k = coef_k + 2 x b_{k+1} - b_{k+2} (k = Kc-1 .. 1),  f = coef_0 + x b_1 - b_2,
+// with the function's coefficients staged in shared memory.
+__global__ void plain_g_cheb_kernel(int M, int Q, const double *__restrict__ coef, int Kc,
+                                    const double *__restrict__ omt2, const double *__restrict__ wq,
+                                    double *__restrict__ G, int ldg)
+{
+    extern __shared__ double cs[];
+    const int b = blockIdx.y;
+    for (int k = threadIdx.x; k < Kc; k += blockDim.x) cs[k] = coef[(size_t)b * Kc + k];
+    __syncthreads();
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j > M / 2) return;
+    const double s = sinpi((double)j / (double)M);
+    const double u = 2.0 * s * s;
+    double acc = 0.0;
+    for (int q = 0; q < Q; ++q) {
+        const double x = 1.0 - u * omt2[q];
+        double b1 = 0.0, b2 = 0.0;
+        for (int k = Kc - 1; k >= 1; --k) {
+            const double t = fma(2.0 * x, b1, cs[k] - b2);
+            b2 = b1;
+            b1 = t;
+        }
+        acc += wq[q] * fma(x, b1, cs[0] - b2);
+    }
+    G[(size_t)b * ldg + j] = acc;
+}
+
 }  // namespace
+
+int leg_plain_g_cheb(const leg_plan *p, const double *coef, int Kc, int B, double *G, int ldg, cudaStream_t st)
+{
+    if (B == 0) return LEG_OK;
+    const size_t smem = sizeof(double) * (size_t)Kc;
+    if (smem > 48 * 1024)
+        LEG_CUDA_TRY(cudaFuncSetAttribute(plain_g_cheb_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    dim3 grid((p->rows + 127) / 128, B);
+    plain_g_cheb_kernel<<<grid, 128, smem, st>>>(p->M, p->Q, coef, Kc, p->omt2, p->wq, G, ldg);
+    LEG_LAUNCH_CHECK("plain_g_cheb_kernel");
+    return LEG_OK;
+}
 
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,
                 cudaStream_t st)

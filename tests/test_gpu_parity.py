@@ -68,6 +68,26 @@ def test_plain_method_exponential(leg, oracle):
         assert relerr(c[i], ref) < 1e-12
 
 
+def test_plain_method_chebyshev_series(leg, oracle):
+    """The third ragged family on the plain path: f = sum_m g_m rho^m T_m
+    evaluated at the quadrature points (Clenshaw) against route 2 with the same
+    closed form (numpy's chebval), and, the rule being exact for degree 40 and
+    M > N + 40, against the exact Legendre coefficients of route 1."""
+    N, M, Q, Kc = 48, 256, 24, 41
+    plan = leg.Plan(N, M, 2, Q, leg.F64)
+    rng = np.random.default_rng(31)
+    coef = np.array([rng.standard_normal(Kc) * r ** np.arange(Kc) for r in (0.5, 0.9, 0.99)])
+    c = plan.plain_forward_cheb(torch.tensor(coef, device="cuda")).cpu().numpy()
+    plan.status()
+    for i in range(coef.shape[0]):
+        ref = oracle.coeffs_abel(N, M, Q, f=lambda omx: np.polynomial.chebyshev.chebval(1 - omx, coef[i]))[0]
+        assert relerr(c[i], ref) < 1e-12
+        exact = oracle.coeffs_direct(N, 64, f=lambda x: np.polynomial.chebyshev.chebval(x, coef[i]))[0]
+        assert relerr(c[i], exact) < 1e-12
+    with pytest.raises(leg.LegError):
+        plan.plain_forward_cheb(torch.zeros((1, 16385 + 1), dtype=torch.float64, device="cuda"))
+
+
 @pytest.mark.parametrize("sym", [True, False])
 def test_plain_method_literal_and_symmetric_rules(leg, oracle, sym):
     N, M, Q = 32, 128, 11
