@@ -73,7 +73,6 @@ namespace {
 constexpr int CTA_M = 128;                          // operator rows per CTA (TMEM lanes)
 constexpr int PAIR_M = 2 * CTA_M;                   // MMA M of a CTA pair
 constexpr int TILE_K = 32;                          // K per stage: 64-byte FP16 rows
-constexpr int MAX_TN = 256;                         // functions per pair tile, at most (BF16)
 constexpr int ATILE_BYTES = CTA_M * TILE_K * 2;     // 8 KB per operator plane
 constexpr int CHUNK_KB = 4;                         // K blocks per accumulation chunk of acc1
 constexpr int MAX_STAGES = 8;
