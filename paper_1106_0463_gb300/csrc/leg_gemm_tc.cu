@@ -742,7 +742,7 @@ int get_encoder(EncodeTiledFn *fn)
 int make_map(CUtensorMap *m, const void *base, int inner, int outer, int ld, int planes, size_t pstride, bool bf16,
              int box_outer)
 {
-    EncodeTiledFn enc;
+    EncodeTiledFn enc = nullptr;
     int rc = get_encoder(&enc);
     if (rc) return rc;
     cuuint64_t dims[3] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)planes};
