@@ -7,7 +7,7 @@
  * only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg load it.
  * It shares no code, header or table with the CUDA library.
  *
- * Two independent routes to the coefficients c_n of f(x) = sum_n c_n P_n(x):
+ * Independent routes to the coefficients c_n of f(x) = sum_n c_n P_n(x):
  *
  *   Route 1 (plain definition, Eq. 2.3):
  *       c_n = (n + 1/2) * integral_{-1}^{1} f(x) P_n(x) dx,
@@ -27,6 +27,15 @@
  *     - fhat(y) = eps(y) e^{i y/2} phi(y) / (2 pi i)   (Eq. 2.5);
  *     - a_n = (2 pi / M) sum_j fhat(y_j) e^{i n y_j}    (Eq. 2.4, trapezoid),
  *       as a direct O(M N) sum (no FFT), and c_n = (2n+1) a_n.
+ *
+ *   Route 3 (the half-range sine form, Eq. 2.13 with phi of Eq. 2.14):
+ *       c_n = (2/pi) (n + 1/2) int_0^pi phi(y) sin((n + 1/2) y) dy
+ *     on y_j = pi j / L, j = 0..L, by the trapezoid rule, phi from the same
+ *     substitution as route 2, the sine sum written out directly.
+ *
+ *   Route 1 transposed (or_coeffs_quadrature_T, or_cl_barycentric_T): the
+ *   adjoint df = L^T v of the route-1 map on sampled inputs, for checks of
+ *   the library's adjoint at sizes where explicit operators are too large.
  *
  * Sampled inputs are values f_k at the Chebyshev-Lobatto nodes
  * x_k = cos(pi k / (K-1)), k = 0..K-1 (x_0 = 1 down to x_{K-1} = -1), and are
@@ -349,4 +358,142 @@ void or_twisted_dft_matrix(int N, int M, double *R)
     free(e);
     free(cre);
     free(cim);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Route 3: the half-range sine form of the coefficients (Eq. 2.13, with phi */
+/* of Eq. 2.14), obtained in the paper from the symmetry Eq. 2.12:           */
+/*   c_n = (2/pi) (n + 1/2) int_0^pi phi(y) sin((n + 1/2) y) dy,             */
+/* on the grid y_j = pi j / L, j = 0..L, by the trapezoid rule (end points   */
+/* at half weight), phi from the same substitution as route 2:               */
+/*   phi(y) = 2 sin(y/2) int_0^1 f(1 - 2 sin^2(y/2)(1 - tau^2)) dtau.        */
+/* Step 1: the quadrature points, omx: (L+1) x Q.                            */
+/* ------------------------------------------------------------------------ */
+void or_sine_points(int L, int Q, int sym, double *omx, double *wq)
+{
+    double *tau = (double *)malloc(sizeof(double) * Q);
+    double *omt2 = (double *)malloc(sizeof(double) * Q);
+    or_tau_rule(Q, sym, tau, wq, omt2);
+    for (int j = 0; j <= L; ++j) {
+        double s = sin(0.5 * M_PI * j / L);
+        double u = 2.0 * s * s;
+        for (int q = 0; q < Q; ++q) omx[(size_t)j * Q + q] = u * omt2[q];
+    }
+    free(tau);
+    free(omt2);
+}
+
+/* Step 2: phi(y_j) = 2 sin(y_j/2) sum_q w_q f(x_jq), y_j in [0, pi].        */
+/* fq: B x (L+1) x Q, phi: B x (L+1).                                        */
+void or_sine_phi(int L, int Q, int B, const double *fq, const double *wq, double *phi)
+{
+    #pragma omp parallel for schedule(static)
+    for (int b = 0; b < B; ++b) {
+        for (int j = 0; j <= L; ++j) {
+            const double *row = fq + ((size_t)b * (L + 1) + j) * Q;
+            double g = 0.0;
+            for (int q = 0; q < Q; ++q) g += wq[q] * row[q];
+            phi[(size_t)b * (L + 1) + j] = 2.0 * sin(0.5 * M_PI * j / L) * g;
+        }
+    }
+}
+
+/* Step 3: the sine sum of Eq. 2.13, direct (no fast transform).             */
+/* phi: B x (L+1); c: B x N.                                                 */
+void or_sine_coeffs(int N, int L, int B, const double *phi, double *c)
+{
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < B; ++b) {
+        const double *pb = phi + (size_t)b * (L + 1);
+        for (int n = 0; n < N; ++n) {
+            double s = 0.0;
+            for (int j = 0; j <= L; ++j) {
+                /* sin((n + 1/2) pi j / L) = sin(pi (2n+1) j / (2L)); the     */
+                /* angle is reduced exactly through the integer (2n+1) j mod 4L */
+                long long r = ((long long)(2 * n + 1) * j) % (4LL * L);
+                double w = (j == 0 || j == L) ? 0.5 : 1.0;
+                s += w * pb[j] * sin(M_PI * (double)r / (2.0 * L));
+            }
+            c[(size_t)b * N + n] = (2.0 / M_PI) * (n + 0.5) * (M_PI / L) * s;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Route 1 transposed, for checks of the adjoint df = L^T v of sampled      */
+/* inputs.  Route 1 on CL samples is c = P (W (B f)), with B the barycentric */
+/* interpolation to the Gauss points, W the Gauss weights and                */
+/* P[n, i] = (n + 1/2) P_n(x_i) (Eq. 2.3).  Its transpose is applied in two */
+/* steps:                                                                    */
+/*   u_i = wts_i sum_n (n + 1/2) v_n P_n(x_i)        (or_coeffs_quadrature_T) */
+/*   df_k = sum_i l_k(x_i) u_i                       (or_cl_barycentric_T)    */
+/* v: B x N, u: B x npts.                                                    */
+/* ------------------------------------------------------------------------ */
+void or_coeffs_quadrature_T(int N, int npts, const double *x, const double *wts,
+                            int B, const double *v, double *u)
+{
+    double *P = (double *)malloc(sizeof(double) * (size_t)N * npts);
+    or_legendre_table(N, npts, x, P);
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int b = 0; b < B; ++b) {
+        const double *vb = v + (size_t)b * N;
+        double *ub = u + (size_t)b * npts;
+        for (int i = 0; i < npts; ++i) ub[i] = 0.0;
+        for (int n = 0; n < N; ++n) {
+            const double *Pn = P + (size_t)n * npts;
+            const double a = (n + 0.5) * vb[n];
+            for (int i = 0; i < npts; ++i) ub[i] += a * Pn[i];
+        }
+        for (int i = 0; i < npts; ++i) ub[i] *= wts[i];
+    }
+    free(P);
+}
+
+/* df[b, k] = sum_i l_k(x_i) u[b, i], x_i given by omx = 1 - x_i; the same   */
+/* barycentric weights and node-hit rule as or_cl_barycentric.               */
+void or_cl_barycentric_T(int K, int B, const double *u, int npts, const double *omx, double *df)
+{
+    double *omxk = (double *)malloc(sizeof(double) * K);
+    double *lam = (double *)malloc(sizeof(double) * K);
+    for (int k = 0; k < K; ++k) {
+        double s = sin(M_PI * k / (2.0 * (K - 1)));
+        omxk[k] = 2.0 * s * s;
+        lam[k] = (k % 2 == 0) ? 1.0 : -1.0;
+    }
+    lam[0] *= 0.5;
+    lam[K - 1] *= 0.5;
+    memset(df, 0, sizeof(double) * (size_t)B * K);
+    #pragma omp parallel
+    {
+        double *t = (double *)malloc(sizeof(double) * K);
+        double *acc = (double *)calloc((size_t)B * K, sizeof(double));
+        #pragma omp for schedule(dynamic, 8)
+        for (int i = 0; i < npts; ++i) {
+            int hit = -1;
+            double den = 0.0;
+            for (int k = 0; k < K; ++k) {
+                double d = omxk[k] - omx[i];
+                if (d == 0.0) { hit = k; break; }
+                t[k] = lam[k] / d;
+                den += t[k];
+            }
+            for (int b = 0; b < B; ++b) {
+                double ui = u[(size_t)b * npts + i];
+                double *ab = acc + (size_t)b * K;
+                if (hit >= 0) {
+                    ab[hit] += ui;
+                } else {
+                    for (int k = 0; k < K; ++k) ab[k] += (t[k] / den) * ui;
+                }
+            }
+        }
+        #pragma omp critical
+        {
+            for (size_t e = 0; e < (size_t)B * K; ++e) df[e] += acc[e];
+        }
+        free(acc);
+        free(t);
+    }
+    free(omxk);
+    free(lam);
 }

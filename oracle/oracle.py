@@ -13,6 +13,11 @@ Routes (De Micheli & Viano, arXiv:1106.0463):
   x = cos y + s^2 and the s-integral taken by Gauss-Legendre (Sec. 2, the
   paragraph after Eq. 2.14), then the Fourier sum of Eq. 2.4 written out
   directly (no FFT).
+* :func:`coeffs_sine` -- route 3, the half-range sine form Eq. 2.13 with phi
+  of Eq. 2.14 on y_j = pi j / L, j = 0..L (L = M/2), trapezoid rule, the
+  sine sum written out directly.
+* :func:`adjoint_direct` -- route 1 transposed: df = L^T v for sampled
+  inputs, for checks of the adjoint.
 
 Sampled inputs are values at the Chebyshev-Lobatto nodes
 x_k = cos(pi k / (K-1)), k = 0..K-1, read through their barycentric
@@ -68,6 +73,11 @@ def _load():
                 "or_abel_coeffs": [i, i, i, p, p, p],
                 "or_abel_operator": [i, i, i, i, p],
                 "or_twisted_dft_matrix": [i, i, p],
+                "or_sine_points": [i, i, i, p, p],
+                "or_sine_phi": [i, i, i, p, p, p],
+                "or_sine_coeffs": [i, i, i, p, p],
+                "or_coeffs_quadrature_T": [i, i, p, p, i, p, p],
+                "or_cl_barycentric_T": [i, i, p, i, p, p],
             }
             for name, argt in sig.items():
                 fn = getattr(lib, name)
@@ -227,6 +237,63 @@ def twisted_dft_matrix(N: int, M: int) -> np.ndarray:
     R = np.empty((N, M))
     _load().or_twisted_dft_matrix(N, M, _ptr(R))
     return R
+
+
+def sine_points(L: int, Q: int, sym: bool = True):
+    """1 - x_jq = 2 sin^2(y_j/2)(1 - tau_q^2) on y_j = pi j / L, j = 0..L; shape (L+1, Q); and w_q."""
+    omx = np.empty((L + 1, Q))
+    wq = np.empty(Q)
+    _load().or_sine_points(L, Q, int(bool(sym)), _ptr(omx), _ptr(wq))
+    return omx, wq
+
+
+def sine_phi(fq, wq) -> np.ndarray:
+    """phi(y_j) = 2 sin(y_j/2) sum_q w_q f(x_jq) on [0, pi] (Eq. 2.14); fq: (B, L+1, Q)."""
+    fq = _f64(fq)
+    B, L1, Q = fq.shape
+    phi = np.empty((B, L1))
+    _load().or_sine_phi(L1 - 1, Q, B, _ptr(fq), _ptr(_f64(wq)), _ptr(phi))
+    return phi
+
+
+def sine_coeffs(N: int, phi) -> np.ndarray:
+    """Eq. 2.13 by the trapezoid rule on y_j = pi j / L, direct sine sum; phi: (B, L+1)."""
+    phi = _f64(np.atleast_2d(phi))
+    B, L1 = phi.shape
+    c = np.empty((B, N))
+    _load().or_sine_coeffs(N, L1 - 1, B, _ptr(phi), _ptr(c))
+    return c
+
+
+def coeffs_sine(N: int, M: int, Q: int, *, sym: bool = True, f=None, f_cl=None) -> np.ndarray:
+    """Route 3: the half-range sine form (Eqs. 2.13, 2.14) on L = M/2 intervals of [0, pi].
+
+    ``f`` is a closed form of (1 - x) evaluated at the quadrature points (the
+    plain method); ``f_cl`` are CL samples read through the barycentric
+    interpolant."""
+    L = M // 2
+    omx, wq = sine_points(L, Q, sym)
+    if f_cl is not None:
+        f_cl = np.atleast_2d(f_cl)
+        fq = cl_barycentric(f_cl, omx.ravel()).reshape(f_cl.shape[0], L + 1, Q)
+    else:
+        fq = np.asarray(f(omx), dtype=np.float64).reshape(-1, L + 1, Q)
+    return sine_coeffs(N, sine_phi(fq, wq))
+
+
+def adjoint_direct(Qo: int, K: int, v) -> np.ndarray:
+    """df = L^T v for the route-1 map on K CL samples with a Qo-point Gauss rule:
+    u_i = w_i sum_n (n + 1/2) v_n P_n(x_i), then df_k = sum_i l_k(x_i) u_i.
+    v: (B, N); returns (B, K)."""
+    v = _f64(np.atleast_2d(v))
+    B, N = v.shape
+    x, w = gauss_legendre(Qo)
+    u = np.empty((B, Qo))
+    _load().or_coeffs_quadrature_T(N, Qo, _ptr(x), _ptr(w), B, _ptr(v), _ptr(u))
+    omx = _f64(1.0 - x)
+    df = np.empty((B, K))
+    _load().or_cl_barycentric_T(K, B, _ptr(u), Qo, _ptr(omx), _ptr(df))
+    return df
 
 
 def exact_tau_points(K: int) -> int:

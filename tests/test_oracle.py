@@ -299,3 +299,95 @@ def test_explicit_operators_reproduce_route2(oracle):
     phi = A @ sp.eval_legendre(m, xk)
     y = -np.pi + 2 * np.pi * np.arange(M) / M
     assert np.max(np.abs(phi - 2 * np.sin((m + 0.5) * np.abs(y)) / (2 * m + 1))) < 1e-14
+
+
+# ---------------------------------------------------------------- route 3 (Eq. 2.13)
+@pytest.mark.parametrize("sym", [True, False])
+def test_route3_plain_method_generating_function(oracle, sym):
+    # the sine form of Eq. 2.13 on [0, pi]: c_n = 0.5^n to 1e-12 at the plain
+    # method's sizes (Eq. 2.2)
+    cfg = workloads.CONFIGS["genfn_plain_n64"]
+    t = cfg["t"]
+    c = oracle.coeffs_sine(cfg["N"], cfg["M"], cfg["Q"], sym=sym,
+                           f=lambda omx: (1 - 2 * (1 - omx) * t + t * t) ** -0.5)[0]
+    assert np.max(np.abs(c - t ** np.arange(cfg["N"]))) < 1e-12
+
+
+def test_route3_phi_of_legendre_polynomial(oracle):
+    # Eq. 2.14 for f = P_m on [0, pi]: phi(y) = 2 sin((m + 1/2) y) / (2m + 1)
+    L = 64
+    for m in (0, 2, 9, 31):
+        Q = m // 2 + 2
+        omx, wq = oracle.sine_points(L, Q, True)
+        phi = oracle.sine_phi(sp.eval_legendre(m, 1 - omx)[None], wq)[0]
+        y = np.pi * np.arange(L + 1) / L
+        assert np.max(np.abs(phi - 2 * np.sin((m + 0.5) * y) / (2 * m + 1))) < 1e-14
+
+
+def test_route3_legendre_polynomial_gives_delta(oracle):
+    N, M = 24, 128
+    for m in (0, 5, 23):
+        c = oracle.coeffs_sine(N, M, 16, f=lambda omx: sp.eval_legendre(m, 1 - omx))[0]
+        e = np.zeros(N)
+        e[m] = 1.0
+        assert np.max(np.abs(c - e)) < 1e-13
+
+
+def test_route3_exponential(oracle):
+    # c_n = (2n+1) i_n(a) for e^{ax}
+    N, M, Q = 40, 256, 40
+    for a in (-4.0, 1.5):
+        c = oracle.coeffs_sine(N, M, Q, f=lambda omx: np.exp(a * (1 - omx)))[0]
+        n = np.arange(N)
+        ref = (2 * n + 1) * sp.spherical_in(n, a)
+        assert np.max(np.abs(c - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+def test_route3_equals_route2_on_sampled_inputs(oracle):
+    # the half-range sine form and the full-range Fourier sum are the same
+    # discrete map (symmetry Eq. 2.12 on the grid): route 3 = route 2 to
+    # rounding on random series at non-exact (M, Q)
+    rng = np.random.default_rng(17)
+    K, N, M, Q = 97, 60, 256, 20
+    coef = rng.standard_normal((3, K)) * 0.93 ** np.arange(K)
+    xk, _ = oracle.cl_nodes(K)
+    fk = np.stack([chebval(xk, c) for c in coef])
+    c2 = oracle.coeffs_abel(N, M, Q, f_cl=fk)
+    c3 = oracle.coeffs_sine(N, M, Q, f_cl=fk)
+    assert np.max(np.abs(c3 - c2)) < 1e-13 * np.max(np.abs(c2))
+
+
+def test_route3_table1_converges(oracle):
+    # |x|^{3/2}: at M = 1024, Q = 512 within 1e-6 of Table 1's true column
+    rows = _table1()
+    c = oracle.coeffs_sine(32, 1024, 512, f=lambda omx: np.abs(1 - omx) ** 1.5)[0]
+    assert max(abs(c[n] - float(t)) for n, t, _ in rows) < 1e-6
+    assert np.max(np.abs(c[1::2])) < 1e-6
+
+
+# ---------------------------------------------------------------- route 1 transposed
+def test_adjoint_direct_dot_product_identity(oracle):
+    # <L f, v> = <f, L^T v> with L f from route 1 (Eq. 2.3) on CL samples
+    rng = np.random.default_rng(21)
+    for K, N, Qo in ((9, 5, 12), (65, 48, 60), (129, 100, 120)):
+        f = rng.standard_normal((3, K))
+        v = rng.standard_normal((3, N))
+        c = oracle.coeffs_direct(N, Qo, f_cl=f)
+        df = oracle.adjoint_direct(Qo, K, v)
+        lhs = np.sum(c * v, axis=1)
+        rhs = np.sum(f * df, axis=1)
+        assert np.max(np.abs(lhs - rhs)) < 1e-12 * np.max(np.abs(c) @ np.abs(v).T)
+
+
+def test_adjoint_direct_equals_explicit_route2_transpose(oracle):
+    # exact configuration (M > N + K - 1, exact tau rule): the explicit route-2
+    # operators give the same map, so (R A)^T v equals route 1 transposed
+    rng = np.random.default_rng(22)
+    K, N, M = 17, 12, 32
+    Q = oracle.exact_tau_points(K)
+    A = oracle.abel_operator(M, K, Q, True)
+    R = oracle.twisted_dft_matrix(N, M)
+    v = rng.standard_normal((4, N))
+    ref = v @ (R @ A)
+    df = oracle.adjoint_direct((K + N) // 2 + 2, K, v)
+    assert np.max(np.abs(df - ref)) < 1e-12 * np.max(np.abs(ref))
