@@ -1,25 +1,35 @@
 """Throughput benchmark of the Legendre-coefficient path on GB300.
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--workload NAME] [--path split_fp16|f32|bf16|f64]
+                [--workload NAME] [--path split_fp16|f32|bf16|f64] [--no-extras]
 
 One step = one forward pass of the sampled-input path over one batch with
-inputs resident in HBM: input split -> tcgen05 Abel GEMM -> twisted FFT with
-the (2n+1) scaling (leg_forward).  The default workload is B=4096 random
-decaying Chebyshev series at K=1025 Chebyshev-Lobatto nodes, N=512
-coefficients, M=2048 trapezoid points (exact tau rule), on the split-FP16 path
-whose error against the FP64 oracle is measured in the same run.
+inputs resident in HBM: input split -> tcgen05 Abel GEMM -> transform with the
+(2n+1) scaling (leg_forward).  The headline workload is the largest dense
+single-GPU configuration: B=256 random decaying Chebyshev series at K=8193
+Chebyshev-Lobatto nodes, N=4096 coefficients, M=16384 trapezoid points (exact
+tau rule), on the split-FP16 path, its error against the FP64 oracle measured
+in the same run on sampled functions (the first and last of every function
+tile of the GEMM among them).
+
+The same JSON line carries, under "workloads", every other configuration of
+the method with its own error against the oracle, time and roofline: the
+plain method (one function, c_n = 0.5^n checked to 1e-12), B=4096 at K=1025
+(split-FP16, plain FP32, FP64, collapsed operator), the ragged batch of
+10,000 closed-form functions, the differentiation workload (forward +
+backward, with the FP64 GPU path's time beside it), the precision sweep of
+the headline workload (FP64, FP32, BF16 next to split-FP16), the sine-form
+transform (Eq. 2.13) on the headline workload, and Table 1's |x|^{3/2} on
+the plain method at several (M, Q).
 
 Timing: W untimed warm-up steps; then, for each of K steps, L2 is flushed
-(a 512 MiB write) and the step is timed with CUDA events recorded by the
-library on the launch stream between its stages (leg_forward_profiled).
-Barrier + synchronize bracket the timed steps; the max over ranks is taken.
-Under torchrun (N > 1) every rank runs its own batch (weak scaling, no
-collective on the data path).
+(a 512 MiB write) and the step is timed with CUDA events on the launch
+stream.  Barrier + synchronize bracket the timed steps; the max over ranks is
+taken.  Under torchrun (N > 1) every rank runs its own batch (weak scaling,
+no collective on the data path).
 
---impl reference times the FP64 CPU oracle (the paper's method written out
-directly, route 2) on the host cores, on a bounded sample of the same
-workload per step.
+--impl reference times the FP64 CPU oracle on the host cores, on a bounded
+sample of the same workload per step.
 """
 from __future__ import annotations
 
@@ -41,18 +51,19 @@ import workloads  # noqa: E402
 
 METRIC = "Legendre coeffs/sec (B*N/s) at <=1e-6 rel err vs FP64 oracle; % roofline vs plain FP64"
 UNIT = "coeffs/s"
+HEADLINE = "cheb_b256_k8193_n4096_m16384"
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="cheb_b4096_k1025_n512_m2048")
+    ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--path", default="split_fp16", choices=["split_fp16", "f32", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the FP64/FP32 comparison paths")
+    ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     return ap.parse_args()
 
 
@@ -134,28 +145,57 @@ def parse_clocks(path: str):
 
 
 # ------------------------------------------------------------------ oracle (CPU)
-def oracle_rate(name: str, seconds: float = 12.0, max_fns: int = 256):
-    """Route 2 of the FP64 oracle on a bounded sample of the workload."""
+def host_cores() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+
+
+def exact_config(name: str) -> bool:
+    """M > N + K - 1 with the exact tau rule: the discrete method has no
+    discretisation error on these sampled inputs and the oracle's route 1
+    (Eq. 2.3) and route 2 (Theorem 1) agree to rounding."""
+    cfg = workloads.CONFIGS[name]
+    return cfg["M"] > cfg["N"] + cfg["K"] - 1
+
+
+def oracle_quadrature_points(cfg) -> int:
+    """Gauss points of route 1 that integrate f P_n exactly for n < N on the
+    degree-(K-1) interpolant."""
+    return (cfg["K"] + cfg["N"]) // 2 + 4
+
+
+def oracle_coeffs(O, name, f):
+    """Oracle coefficients of the sampled functions f (rows, FP64): route 1 on
+    the exact configurations, route 2 otherwise."""
+    cfg = workloads.CONFIGS[name]
+    if exact_config(name):
+        return O.coeffs_direct(cfg["N"], oracle_quadrature_points(cfg), f_cl=f)
+    return O.coeffs_abel(cfg["N"], cfg["M"], O.exact_tau_points(cfg["K"]), f_cl=f)
+
+
+def oracle_route_name(name):
+    return ("route 1 (Eq. 2.3, %d-point Gauss rule; the configuration is exact, so routes 1 and 2 agree to "
+            "rounding)" % oracle_quadrature_points(workloads.CONFIGS[name]) if exact_config(name)
+            else "route 2 (Abel + trapezoid, direct Fourier sum)")
+
+
+def oracle_rate(name: str, seconds: float = 10.0, max_fns: int = 256):
+    """The oracle as it stands on a bounded sample of the workload (about
+    `seconds` of CPU work), in coefficients per second."""
     from oracle import oracle as O
     cfg = workloads.CONFIGS[name]
-    N, M, K = cfg["N"], cfg["M"], cfg["K"]
-    Q = O.exact_tau_points(K)
     f = workloads.workload_inputs(name).astype(np.float64)
     n = 2
     t0 = time.time()
-    O.coeffs_abel(N, M, Q, f_cl=f[:n])
+    oracle_coeffs(O, name, f[:n])
     dt = time.time() - t0
-    # the cost is dominated by the per-point barycentric weights (shared by the
-    # functions of one call), so grow the sample while it fits the budget
     while dt < seconds / 3 and n < max_fns:
         n = min(max_fns, n * 4)
         t0 = time.time()
-        O.coeffs_abel(N, M, Q, f_cl=f[:n])
+        oracle_coeffs(O, name, f[:n])
         dt = time.time() - t0
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": n * N / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d of %d functions of %s, oracle route 2 (Abel + trapezoid, direct Fourier sum), "
-                      "FP64, OpenMP, %.2f s" % (n, cfg["B"], name, dt)}, n, dt
+    return {"value": n * cfg["N"] / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": "%d of %d functions of %s, oracle %s, FP64, OpenMP, %.2f s"
+                      % (n, cfg["B"], name, oracle_route_name(name), dt)}, n, dt
 
 
 def reference_arm(args, rank, world):
@@ -164,45 +204,44 @@ def reference_arm(args, rank, world):
     name = args.workload
     cfg = workloads.CONFIGS[name]
     from oracle import oracle as O
-    N, M, K = cfg["N"], cfg["M"], cfg["K"]
-    Q = O.exact_tau_points(K)
     f = workloads.workload_inputs(name).astype(np.float64)
-    # size one step to about 2 s of CPU work, and all steps to about a minute
-    base, n, dt = oracle_rate(name, seconds=6.0, max_fns=64)
+    # one step is a bounded sample (about 2 s of CPU work, less for many steps)
+    base, n, dt = oracle_rate(name, seconds=4.0, max_fns=64)
     per_fn = dt / n
     budget = min(2.0, 60.0 / max(1, args.steps + args.warmup))
     S = max(1, min(cfg["B"], int(budget / max(per_fn, 1e-9))))
     for _ in range(args.warmup):
-        O.coeffs_abel(N, M, Q, f_cl=f[:S])
+        oracle_coeffs(O, name, f[:S])
     times = []
     for i in range(args.steps):
         lo = (i * S) % max(1, cfg["B"] - S + 1)
         t0 = time.perf_counter()
-        O.coeffs_abel(N, M, Q, f_cl=f[lo:lo + S])
+        oracle_coeffs(O, name, f[lo:lo + S])
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
-    value = S * N / (ms / 1e3)
-    cores = base["cores"]
+    value = S * cfg["N"] / (ms / 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": name, "B": cfg["B"], "K": K, "N": N, "M": M, "Q": Q,
-                   "path": "oracle route 2 (CPU)", "sample_per_step": S},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+        "config": {"workload": name, "B": cfg["B"], "K": cfg["K"], "N": cfg["N"], "M": cfg["M"],
+                   "Q": O.exact_tau_points(cfg["K"]), "path": "FP64 CPU oracle, " + oracle_route_name(name),
+                   "sample_per_step": S},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": base["cores"], "kind": "oracle",
                          "sample": "%d functions per step of %s" % (S, name)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 
 
-# ------------------------------------------------------------------ GPU arm
+# ------------------------------------------------------------------ rooflines
 PATHS = {"split_fp16": 3, "f32": 1, "bf16": 2, "f64": 0}
 DTYPE_STR = {
     "split_fp16": "f16 split (8 tcgen05 products, f32 accum, exact leading accumulator) + df32 FFT",
     "f32": "f32", "bf16": "bf16 (f32 accum) + f32 FFT", "f64": "f64",
 }
-
+PRODUCTS = {"split_fp16": 8, "bf16": 1, "f32": 1, "f64": 1}
+LAUNCHES = {"split_fp16": 3, "bf16": 3, "f32": 2, "f64": 2}
 
 # Peak arithmetic rates of the FFT stage (ops/s in units of 1e12), from unit
 # counts and clocks: 152 SMs x 128 FP32 lanes x 2.07 GHz (one FP32 add, mul or
@@ -210,16 +249,14 @@ DTYPE_STR = {
 ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 
 # DRAM bytes (read + write) per launch measured by ncu for the current kernels
-# (one ncu capture per kernel); keyed by (stage, path, workload).
-TRAFFIC = {
-    ("abel_gemm", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 69294080,   # tc_gemm_pair_split_fp16_...
-    ("fft", "split_fp16", "cheb_b4096_k1025_n512_m2048"): 34181120,         # dct16_forward_dfl_...
-}
+# (one ncu capture per kernel, summaries under profiles/); keyed by
+# (stage, path, workload).  A kernel changed since its capture has no entry.
+TRAFFIC = {}
 
 
 def fft_fp32_ops(M, N):
-    """FP32 operations of the double-float transform of one function (the
-    algorithmic operation count of the method's FFT stage at the precision it
+    """FP32 operations of the double-float real-even transform of one function
+    (the algorithmic operation count of the FFT stage at the precision it
     needs): a length-H complex FFT (H = M/4) with (H/2) log2 H radix-2
     butterflies of 4 mul + 6 add, the fold (L = M/2 values: 3.5 add + 2.5 mul
     each), the recombination (H x 8 add + 4 mul), the scan (H add) and the
@@ -232,60 +269,93 @@ def fft_fp32_ops(M, N):
     return 8 * adds + 4 * muls
 
 
+def dst_fp32_ops(M, N):
+    """FP32 operations of the double-float sine-form transform (Eq. 2.13) of
+    one function, same conventions: the length-H FFT, the merged pre-twiddle
+    (two W values per k < H: 3 add + 2 mul each; their sum and difference:
+    4 add; the twiddle product: 4 mul + 2 add; 2 add) and the output (N x 2
+    mul)."""
+    H = M // 4
+    lg = int(round(np.log2(H)))
+    adds = 3 * H * lg + 14 * H
+    muls = 2 * H * lg + 8 * H + 2 * N
+    return 8 * adds + 4 * muls
+
+
 def relerr(c, ref):
+    """max over functions of max_n |c - c_ref| / max_n |c_ref|."""
+    c = np.atleast_2d(np.asarray(c, dtype=np.float64))
     return float(np.max(np.max(np.abs(c - ref), 1) / np.max(np.abs(ref), 1)))
 
 
-def run_path(leg, torch, name, path, rank, steps, warmup, flush, sample_err=0, flags=0, clocks=None):
-    cfg = workloads.CONFIGS[name]
-    B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
-    dt = PATHS[path]
-    t0 = time.time()
-    plan = leg.Plan(N, M, K, 0, dt, flags=flags)
-    torch.cuda.synchronize()
-    plan_s = time.time() - t0
-    f_np = workloads.workload_inputs(name, salt=rank)
-    io = torch.float64 if dt == leg.F64 else torch.float32
-    f = torch.from_numpy(f_np).to(device="cuda", dtype=io)
-    c = torch.empty((B, N), dtype=io, device="cuda")
-    plan.reserve(B)
-    for _ in range(warmup):
-        plan.forward(f, c)
-    torch.cuda.synchronize()
-    # timed steps: one event pair around the whole forward (kernels overlap
-    # through programmatic dependent launch), L2 flushed before each; the
-    # clock sampler runs over exactly these steps
-    if clocks is not None:
-        clocks.start()
-        clocks.wait_first()
-    step_ms = []
-    for _ in range(steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        plan.forward(f, c)
-        e1.record()
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-    clk = clocks.stop() if clocks is not None else None
-    # stage breakdown: events between the kernels (serialises them), separate passes
-    stage = []
-    for _ in range(min(steps, 10)):
-        flush.zero_()
-        stage.append(plan.forward_profiled(f, c))
-    plan.status()
-    out = {"plan": plan, "f": f, "c": c, "f_np": f_np, "plan_s": plan_s, "stage": stage, "step_ms": step_ms,
-           "clk": clk}
-    if sample_err:
-        out["c_sample"] = c[:sample_err].double().cpu().numpy()
-    return out
+def gemm_roofline(B, rows, K, Kp, path, gemm_ms, peaks, peak_src, traffic, name):
+    """The Abel GEMM's roofline: useful FLOP (2 B rows K, the distinct rows of
+    Eq. 2.12) over the CUDA-event stage time against the measured dense
+    tensor peak; executed FLOP of the split products and the algorithmic HBM
+    bytes (operator planes, input planes, G) beside it."""
+    hbm = peaks.get("hbm_gbs", 6767.1)
+    peak = peaks.get("bf16_tflops", 1880.7)
+    useful = 2.0 * B * rows * K
+    gemm_rows = rows - 1 if path == "split_fp16" else rows   # split: row 0 is a00 e_0, done by the split
+    executed = PRODUCTS[path] * 2.0 * B * gemm_rows * Kp
+    n_a = {"split_fp16": 3, "bf16": 1, "f32": 1, "f64": 1}[path]
+    n_f = {"split_fp16": 7, "bf16": 1, "f32": 1, "f64": 1}[path]
+    eb = {"split_fp16": 2, "bf16": 2, "f32": 4, "f64": 8}[path]
+    gb = {"split_fp16": 8, "bf16": 4, "f32": 4, "f64": 8}[path]
+    bytes_ = n_a * gemm_rows * Kp * eb + n_f * B * Kp * eb + B * rows * gb
+    sec = gemm_ms / 1e3
+    tc = path in ("split_fp16", "bf16")
+    if tc:
+        r = {"kernel": "tc_gemm_kernel (Abel GEMM, tcgen05)", "bound": "tensor",
+             "achieved": useful / sec / 1e12, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": "%s bf16_tflops (dense FP16 rate = BF16 rate)" % peak_src}
+    else:
+        fp = {"f32": 152 * 128 * 2 * 2.07e9 / 1e12, "f64": 1.25}[path]
+        r = {"kernel": "simt_gemm_kernel (Abel GEMM, CUDA cores)", "bound": "alu",
+             "achieved": useful / sec / 1e12, "peak": fp, "unit": "TFLOP/s",
+             "peak_source": "derived: FP32 152 SMs x 128 lanes x 2 FLOP x 2.07 GHz; FP64 nominal 1.25 TFLOP/s"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r.update({"ms": gemm_ms, "flops_per_launch": useful, "executed_flops_per_launch": executed,
+              "executed_tflops": executed / sec / 1e12, "executed_frac": executed / sec / 1e12 / r["peak"],
+              "algorithmic_bytes_per_launch": bytes_, "hbm_gbs": bytes_ / sec / 1e9,
+              "hbm_frac": bytes_ / sec / 1e9 / hbm,
+              "traffic": traffic.get(("abel_gemm", path, name))})
+    return r
 
 
-def time_steps(torch, fn, flush, steps, warmup):
-    """Mean CUDA-event time (ms) of fn() over `steps` calls, L2 flushed before each."""
+def fft_roofline(B, M, N, rows, path, fft_ms, peaks, peak_src, traffic, name, sine=False):
+    """The transform stage: bound by FP32 (double-float) or FP64 arithmetic at
+    the precision the split / FP64 paths need, by HBM for the FP32 path."""
+    hbm = peaks.get("hbm_gbs", 6767.1)
+    gbytes = {"split_fp16": 8, "f64": 8, "f32": 4, "bf16": 4}[path]
+    bytes_ = B * rows * gbytes + B * N * (8 if path == "f64" else 4)
+    sec = fft_ms / 1e3
+    hbm_gbs = bytes_ / sec / 1e9
+    kern = "dst16_forward_kernel (sine form)" if sine else "dct16_forward_kernel (real-even)"
+    if path in ("split_fp16", "f64"):
+        ops = (dst_fp32_ops(M, N) if sine else fft_fp32_ops(M, N)) * B
+        peak = ALU_PEAK_TOPS["f64" if path == "f64" else "f32"]
+        r = {"kernel": kern, "bound": "alu", "achieved": ops / sec / 1e12, "peak": peak, "unit": "Tops/s",
+             "ops_per_launch": ops, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"
+             if path != "f64" else "nominal FP64 1.25 TFLOP/s"}
+        r["frac"] = r["achieved"] / peak
+    else:
+        r = {"kernel": kern if sine else "fft_forward_kernel (Stockham, FP32)", "bound": "hbm", "achieved": hbm_gbs,
+             "peak": hbm, "unit": "GB/s", "frac": hbm_gbs / hbm, "peak_source": "%s hbm_gbs" % peak_src}
+    r.update({"ms": fft_ms, "bytes_per_launch": bytes_, "hbm_gbs": hbm_gbs, "hbm_frac": hbm_gbs / hbm,
+              "traffic": traffic.get(("fft_sine" if sine else "fft", path, name))})
+    return r
+
+
+# ------------------------------------------------------------------ GPU helpers
+def time_steps(torch, fn, flush, steps, warmup, clocks=None):
+    """CUDA-event times (ms) of fn() over `steps` calls, L2 flushed before each."""
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
+    if clocks is not None:
+        clocks.start()
+        clocks.wait_first()
     ts = []
     for _ in range(steps):
         flush.zero_()
@@ -295,13 +365,154 @@ def time_steps(torch, fn, flush, steps, warmup):
         e1.record()
         e1.synchronize()
         ts.append(e0.elapsed_time(e1))
-    return statistics.mean(ts)
+    clk = clocks.stop() if clocks is not None else None
+    return ts, clk
 
 
-def extra_workloads(leg, torch, flush, rank):
-    """The other workloads of the method, measured on the split path."""
-    out = {}
-    # ragged batch: 10,000 closed-form functions, N log-uniform in [32, 8192]
+def sample_rows(B, tn, extra, seed):
+    """Functions to check: the first and last of every function tile of width
+    tn, plus `extra` drawn at random."""
+    idx = set()
+    for t0 in range(0, B, tn):
+        idx.add(t0)
+        idx.add(min(B, t0 + tn) - 1)
+    rng = np.random.default_rng(seed)
+    rest = np.setdiff1d(np.arange(B), sorted(idx))
+    if rest.size:
+        idx.update(int(i) for i in rng.choice(rest, size=min(extra, rest.size), replace=False))
+    return np.array(sorted(idx))
+
+
+class Dense:
+    """One dense sampled workload on the GPU: plans per path built from one
+    FP64 operator, resident inputs, and the oracle reference on sampled rows."""
+
+    def __init__(self, leg, torch, name, rank, with_ref, extra=24):
+        self.leg, self.torch, self.name = leg, torch, name
+        cfg = workloads.CONFIGS[name]
+        self.B, self.K, self.N, self.M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
+        self.rows = self.M // 2 + 1
+        self.Kp = (self.K + 31) // 32 * 32
+        self.f_np = workloads.workload_inputs(name, salt=rank)
+        self.plans = {}
+        self.plan_s = {}
+        t0 = time.time()
+        self.plans["split_fp16"] = leg.Plan(self.N, self.M, self.K, 0, leg.SPLIT_FP16)
+        torch.cuda.synchronize()
+        self.plan_s["split_fp16"] = time.time() - t0
+        self.f32 = torch.from_numpy(self.f_np).cuda()
+        self.tn = self.plans["split_fp16"].tile_info(self.B)["tn"]
+        self.sample = sample_rows(self.B, self.tn, extra, 7 + rank)
+        self.ref = None
+        if with_ref:
+            from oracle import oracle as O
+            self.ref = oracle_coeffs(O, name, self.f_np[self.sample].astype(np.float64))
+
+    def plan(self, path):
+        if path not in self.plans:
+            t0 = time.time()
+            self.plans[path] = self.leg.Plan.like(self.plans["split_fp16"], PATHS[path])
+            self.torch.cuda.synchronize()
+            self.plan_s[path] = time.time() - t0
+        return self.plans[path]
+
+    def inputs(self, path):
+        torch = self.torch
+        if path == "f64":
+            if not hasattr(self, "f64"):
+                self.f64 = self.f32.double()
+            return self.f64
+        return self.f32
+
+    def run(self, path, flush, steps, warmup, peaks, peak_src, clocks=None, transform=None, stages=10):
+        leg, torch = self.leg, self.torch
+        plan = self.plan(path)
+        prev = plan.transform
+        if transform is not None:
+            plan.set_transform(transform)
+        f = self.inputs(path)
+        c = torch.empty((self.B, self.N), dtype=plan.io_dtype, device="cuda")
+        plan.reserve(self.B)
+        ts, clk = time_steps(torch, lambda: plan.forward(f, c), flush, steps, warmup, clocks)
+        st = []
+        for _ in range(min(stages, steps)):
+            flush.zero_()
+            st.append(plan.forward_profiled(f, c))
+        plan.status()
+        ms = float(np.mean(ts))
+        prep_ms, gemm_ms, fft_ms = (float(v) for v in np.mean(np.array(st), 0))
+        out = {"value": self.B * self.N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+               "steps": steps, "plan_build_s": self.plan_s.get(path),
+               "stages_ms": {"input_split": prep_ms, "abel_gemm": gemm_ms, "transform": fft_ms},
+               "gemm_roofline": gemm_roofline(self.B, self.rows, self.K, self.Kp, path, gemm_ms, peaks, peak_src,
+                                              TRAFFIC, self.name),
+               "transform_roofline": fft_roofline(self.B, self.M, self.N, self.rows, path, fft_ms, peaks, peak_src,
+                                                  TRAFFIC, self.name, sine=plan.transform == leg.TRANSFORM_SINE),
+               "gpu_launches_per_step": LAUNCHES[path]}
+        if self.ref is not None:
+            got = c[torch.from_numpy(self.sample).cuda()].double().cpu().numpy()
+            out["max_rel_err"] = relerr(got, self.ref)
+            out["err_sample"] = "%d functions (first and last of every %d-function GEMM tile, the rest random)" \
+                                % (len(self.sample), self.tn)
+        if transform is not None:
+            plan.set_transform(prev)
+        out["_ts"], out["_clk"], out["_stage"] = ts, clk, (prep_ms, gemm_ms, fft_ms)
+        return out
+
+
+def strip(d):
+    return {k: v for k, v in d.items() if not k.startswith("_")}
+
+
+# ------------------------------------------------------------------ other workloads
+def plain_method(leg, torch):
+    """The plain method (closed form at the quadrature points, FP64) on the
+    generating function t = 0.5: c_n = 0.5^n to 1e-12; latency of one call."""
+    cfg = workloads.CONFIGS["genfn_plain_n64"]
+    plan = leg.Plan(cfg["N"], cfg["M"], 17, cfg["Q"], leg.F64)
+    params = torch.tensor([cfg["t"]], dtype=torch.float64, device="cuda")
+    c = torch.empty((1, cfg["N"]), dtype=torch.float64, device="cuda")
+    for _ in range(5):
+        plan.plain_forward(leg.FAMILY_GENFN, params, c)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(50):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.plain_forward(leg.FAMILY_GENFN, params, c)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    err = float(np.max(np.abs(c.cpu().numpy()[0] - cfg["t"] ** np.arange(cfg["N"]))))
+    return {"N": cfg["N"], "M": cfg["M"], "Q": cfg["Q"], "t": cfg["t"], "max_abs_err_vs_t_pow_n": err,
+            "tolerance": 1e-12, "ms_per_call": float(np.median(ts)), "launches_per_call": 2}
+
+
+def table1_plain(leg, torch, O):
+    """Table 1's test function |x|^{3/2} on the plain method with the sine-form
+    transform (Eq. 2.13) at several (M, Q): parity against the oracle's route 3
+    at the same (M, Q), and the method error against the true column (Eq. 2.15)."""
+    true = {}
+    with open(os.path.join(ROOT, "tests", "golden", "table1_abs_x_3_2.txt")) as fh:
+        for line in fh:
+            if line.strip() and not line.startswith("#"):
+                n, t, _ = line.split()
+                true[int(n)] = float(t)
+    out = []
+    N = 32
+    for M, Q in ((256, 64), (1024, 256), (1024, 1024), (4096, 4096)):
+        plan = leg.Plan(N, M, 17, Q, leg.F64, flags=leg.FLAG_SINE_FORM)
+        c = plan.plain_forward(leg.FAMILY_ABSPOW, torch.tensor([1.5], dtype=torch.float64, device="cuda"))
+        got = c.cpu().numpy()[0]
+        ref = O.coeffs_sine(N, M, Q, f=lambda omx: np.abs(1 - omx) ** 1.5)[0]
+        out.append({"M": M, "Q": Q, "parity_vs_oracle_route3": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+                    "max_abs_err_vs_table1_true": max(abs(got[n] - t) for n, t in true.items())})
+    return out
+
+
+def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref):
+    """The ragged workload: 10,000 closed-form functions in 9 size buckets,
+    one grouped persistent GEMM launch, replayed as a CUDA graph."""
     cfg = workloads.CONFIGS["ragged_10000"]
     rng = np.random.default_rng(workloads.SEED_BASE + 3 + 1000 * rank)
     fam, par, n = workloads.ragged_spec(cfg["count"], rng, cfg["Nmin"], cfg["Nmax"])
@@ -317,30 +528,116 @@ def extra_workloads(leg, torch, flush, rank):
                   dev(lay["in_off"], torch.int64), f, coef=dev(lay["coef"], torch.float64),
                   coef_off=dev(lay["coef_off"], torch.int64))
     c = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
-    ms = time_steps(torch, lambda: batch.forward(f, c), flush, 10, 3)
+    ts, _ = time_steps(torch, lambda: batch.forward(f, c), flush, 20, 3)
+    st = []
+    for _ in range(5):
+        flush.zero_()
+        st.append(batch.forward_profiled(f, c))
+    batch.forward(f, c)
     batch.status()
-    out["ragged_10000"] = {"value": float(np.sum(n)) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
-                           "functions": cfg["count"], "coefficients": int(np.sum(n)),
-                           "buckets": lay["buckets"], "plan_build_s": setup,
-                           "launches_per_step": 2 + len(lay["buckets"]), "cuda_graph": True}
+    ms = float(np.mean(ts))
+    split_ms, gemm_ms, fft_ms = (float(v) for v in np.mean(np.array(st), 0))
+    # grouped GEMM roofline: useful FLOP over all buckets
+    useful, executed, abytes = 0.0, 0.0, 0.0
+    for b, Nb in enumerate(lay["buckets"]):
+        N, M, K, Q = workloads.bucket_sizes(Nb)
+        Bb = int(np.sum(lay["bidx"] == b))
+        rows, Kp = M // 2 + 1, (K + 31) // 32 * 32
+        useful += 2.0 * Bb * rows * K
+        executed += 8 * 2.0 * Bb * (rows - 1) * Kp
+        abytes += 3 * (rows - 1) * Kp * 2 + 7 * Bb * Kp * 2 + Bb * rows * 8
+    peak = peaks.get("bf16_tflops", 1880.7)
+    sec = gemm_ms / 1e3
+    roof = {"kernel": "tc_gemm_kernel (grouped Abel GEMM over all buckets)", "bound": "tensor",
+            "achieved": useful / sec / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": useful / sec / 1e12 / peak,
+            "executed_tflops": executed / sec / 1e12, "executed_frac": executed / sec / 1e12 / peak,
+            "flops_per_launch": useful, "executed_flops_per_launch": executed,
+            "algorithmic_bytes_per_launch": abytes, "hbm_gbs": abytes / sec / 1e9,
+            "peak_source": "%s bf16_tflops" % peak_src, "traffic": TRAFFIC.get(("abel_gemm", "split_fp16", "ragged"))}
+    out = {"value": float(np.sum(n)) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "functions": cfg["count"],
+           "coefficients": int(np.sum(n)), "buckets": lay["buckets"], "plan_build_s": setup,
+           "stages_ms": {"input_split": split_ms, "grouped_gemm": gemm_ms, "transforms": fft_ms},
+           "roofline": roof, "tile_width": batch.tile_info()["tn"],
+           "gpu_launches_per_step": 2 + len(lay["buckets"]), "cuda_graph": True}
+    if with_ref:
+        from oracle import oracle as O
+        f_host, c_host = f.cpu().numpy(), c.cpu().numpy()
+        worst, count = 0.0, 0
+        for b, Nb in enumerate(lay["buckets"]):
+            N, M, K, Q = workloads.bucket_sizes(Nb)
+            idx = np.where(lay["bidx"] == b)[0]
+            pick = sorted({int(idx[0]), int(idx[-1])})
+            fk = np.stack([f_host[lay["in_off"][i]:lay["in_off"][i] + K].astype(np.float64) for i in pick])
+            if 2 * Q >= K and M > N + K - 1:
+                refs = O.coeffs_direct(N, (K + N) // 2 + 4, f_cl=fk)
+            else:
+                refs = O.coeffs_abel(N, M, Q, f_cl=fk)
+            for i, r in zip(pick, refs):
+                r = r[:n[i]]
+                g = c_host[lay["out_off"][i]:lay["out_off"][i] + n[i]]
+                worst = max(worst, float(np.max(np.abs(g - r)) / np.max(np.abs(r))))
+                count += 1
+        out["max_rel_err"] = worst
+        out["err_sample"] = ("%d functions, the first and last of every bucket, vs the oracle at the bucket's "
+                             "(N, M, K, Q): route 1 where exact, else route 2" % count)
     del batch, plans, f, c
-    # differentiation workload: forward + backward on the split path
+    return out
+
+
+def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref):
+    """B=1024, K=4097, N=2048, M=8192: forward + backward of the split path
+    (leg_forward, leg_backward) against the FP64 GPU path, errors of both
+    directions against the oracle (route 1 and route 1 transposed)."""
     name = "cheb_b1024_k4097_n2048_m8192"
-    cf = workloads.CONFIGS[name]
-    plan = leg.Plan(cf["N"], cf["M"], cf["K"], 0, leg.SPLIT_FP16)
-    x = torch.from_numpy(workloads.workload_inputs(name)).cuda()
-    cc = torch.empty((cf["B"], cf["N"]), dtype=torch.float32, device="cuda")
+    d = Dense(leg, torch, name, rank, with_ref, extra=12)
+    split = d.plan("split_fp16")
+    f64p = d.plan("f64")
+    B, N, K = d.B, d.N, d.K
+    x = d.f32
+    c = torch.empty((B, N), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(workloads.SEED_BASE + 4 + 1000 * rank)
+    v_np = rng.standard_normal((B, N)).astype(np.float32)
+    v = torch.from_numpy(v_np).cuda()
     df = torch.empty_like(x)
-    plan.reserve(cf["B"])
+    split.reserve(B)
 
     def fwd_bwd():
-        plan.forward(x, cc)
-        plan.backward(cc, df)
-    ms = time_steps(torch, fwd_bwd, flush, 10, 3)
-    plan.status()
-    out["differentiation_b1024_k4097_n2048_m8192"] = {
-        "value": cf["B"] * cf["N"] / (ms / 1e3), "unit": UNIT + " (forward + backward)", "ms_per_step": ms}
-    del plan, x, cc, df
+        split.forward(x, c)
+        split.backward(v, df)
+    ts, _ = time_steps(torch, fwd_bwd, flush, 20, 3)
+    tf, _ = time_steps(torch, lambda: split.forward(x, c), flush, 20, 3)
+    tb, _ = time_steps(torch, lambda: split.backward(v, df), flush, 20, 3)
+    split.status()
+    x64, v64 = x.double(), v.double()
+    c64 = torch.empty((B, N), dtype=torch.float64, device="cuda")
+    df64 = torch.empty_like(x64)
+
+    def fwd_bwd64():
+        f64p.forward(x64, c64)
+        f64p.backward(v64, df64)
+    t64, _ = time_steps(torch, fwd_bwd64, flush, 3, 1)
+    ms, ms64 = float(np.mean(ts)), float(np.mean(t64))
+    out = {"value": B * N / (ms / 1e3), "unit": UNIT + " (forward + backward)", "ms_per_step": ms,
+           "forward_ms": float(np.mean(tf)), "backward_ms": float(np.mean(tb)),
+           "f64_gpu_path": {"value": B * N / (ms64 / 1e3), "ms_per_step": ms64},
+           "speedup_vs_fp64_gpu_path": ms64 / ms, "plan_build_s": d.plan_s.get("split_fp16"),
+           "gpu_launches_per_step": 3 + 3}
+    if with_ref:
+        from oracle import oracle as O
+        sel = torch.from_numpy(d.sample).cuda()
+        split.forward(x, c)
+        out["forward_max_rel_err"] = relerr(c[sel].double().cpu().numpy(), d.ref)
+        split.backward(v, df)
+        ref_b = O.adjoint_direct(oracle_quadrature_points(workloads.CONFIGS[name]), K,
+                                 v_np[d.sample].astype(np.float64))
+        out["backward_max_rel_err"] = relerr(df[sel].double().cpu().numpy(), ref_b)
+        f64p.forward(x64, c64)
+        f64p.backward(v64, df64)
+        out["f64_gpu_path"]["forward_max_rel_err"] = relerr(c64[sel].cpu().numpy(), d.ref)
+        out["f64_gpu_path"]["backward_max_rel_err"] = relerr(df64[sel].cpu().numpy(), ref_b)
+        out["err_sample"] = ("%d functions; forward vs oracle route 1, backward df = L^T v (v ~ N(0,1)) vs the "
+                             "oracle's route 1 transposed" % len(d.sample))
+    del d, split, f64p
     return out
 
 
@@ -372,62 +669,42 @@ def gpu_arm(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     name = args.workload
-    cfg = workloads.CONFIGS[name]
-    B, K, N, M = cfg["B"], cfg["K"], cfg["N"], cfg["M"]
-    rows = M // 2 + 1
     peaks, peak_src = load_peaks()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    with_ref = rank == 0
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    # ---------------- timed region: the selected path
+    # ---------------- the headline: timed region on the selected path
+    head = Dense(leg, torch, name, rank, with_ref, extra=36)
+    B, N = head.B, head.N
     barrier()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local_rank].strip() if vis else str(local_rank)
-    clocks = ClockSampler(phys)
-    res = run_path(leg, torch, name, args.path, rank, args.steps, args.warmup, flush, sample_err=16, clocks=clocks)
+    res = head.run(args.path, flush, args.steps, args.warmup, peaks, peak_src, clocks=ClockSampler(phys))
     barrier()
-    clk = res["clk"]
-    stage = np.array(res["stage"])              # profiled passes x 3 (ms)
-    total_ms = float(np.sum(res["step_ms"]))
-    total_ms = max_over_ranks(torch, dist, total_ms, "cuda")
+    total_ms = max_over_ranks(torch, dist, float(np.sum(res["_ts"])), "cuda")
     ms_per_step = total_ms / args.steps
     value = whole_job_rate(world, B * N, ms_per_step)
-    prep_ms, gemm_ms, fft_ms = (float(v) for v in stage.mean(0))
 
     # ---------------- e2e through the public API with pinned host buffers:
     # leg_forward_host copies f in and c out, overlapped with the computation
-    plan, f, c = res["plan"], res["f"], res["c"]
-    f_host = torch.from_numpy(res["f_np"]).to(f.dtype).pin_memory()
-    c_host = torch.empty(c.shape, dtype=c.dtype).pin_memory()
+    plan = head.plan(args.path)
+    f_host = torch.from_numpy(head.f_np).to(plan.io_dtype).pin_memory()
+    c_host = torch.empty((B, N), dtype=plan.io_dtype).pin_memory()
     st = torch.cuda.current_stream()
-    e2e_ms = []
-    for i in range(args.warmup + args.steps):
-        flush.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(st)
-        plan.forward_host(f_host, c_host, sync=False)
-        e1.record(st)
-        e1.synchronize()
-        if i >= args.warmup:
-            e2e_ms.append(e0.elapsed_time(e1))
-    # the bare copies, for reference (not part of the e2e number)
+    e2e_ts, _ = time_steps(torch, lambda: plan.forward_host(f_host, c_host, sync=False), flush, args.steps,
+                           args.warmup)
+    f_dev = head.inputs(args.path)
+    c_dev = torch.empty((B, N), dtype=plan.io_dtype, device="cuda")
     copy_ms = {}
-    for direction, dst, src in (("h2d", f, f_host), ("d2h", c_host, c)):
-        ts = []
-        for i in range(args.warmup + args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(st)
-            dst.copy_(src, non_blocking=True)
-            e1.record(st)
-            e1.synchronize()
-            if i >= args.warmup:
-                ts.append(e0.elapsed_time(e1))
-        copy_ms[direction] = statistics.mean(ts)
-    e2e_step = max_over_ranks(torch, dist, statistics.mean(e2e_ms), "cuda")
+    for direction, dst, src in (("h2d", f_dev.clone(), f_host), ("d2h", c_host, c_dev)):
+        ts, _ = time_steps(torch, lambda: dst.copy_(src, non_blocking=True), flush, 10, 2)
+        copy_ms[direction] = float(np.mean(ts))
+    e2e_step = max_over_ranks(torch, dist, float(np.mean(e2e_ts)), "cuda")
     e2e = {"value": whole_job_rate(world, B * N, e2e_step), "unit": UNIT,
            "h2d_bytes_per_step": f_host.numel() * f_host.element_size(),
            "d2h_bytes_per_step": c_host.numel() * c_host.element_size(),
@@ -440,110 +717,69 @@ def gpu_arm(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
 
-    # ---------------- parity on sampled functions (oracle, CPU)
-    from oracle import oracle as O
-    ref = O.coeffs_abel(N, M, O.exact_tau_points(K), f_cl=res["f_np"][:16].astype(np.float64))
-    err = relerr(res["c_sample"], ref)
-
-    # ---------------- rooflines (algorithmic work per launch / CUDA-event stage time)
-    Kp = (K + 31) // 32 * 32                               # K padded to the GEMM's 32-wide K blocks
-    flops_useful = 2.0 * B * rows * K                      # per GEMM launch (distinct rows, eq. 2.12)
-    products = {"split_fp16": 8, "bf16": 1, "f32": 1, "f64": 1}[args.path]
-    gemm_rows = rows - 1 if args.path == "split_fp16" else rows   # split: row 0 is a00 e_0, done by the split
-    executed = products * 2.0 * B * gemm_rows * Kp
-    fft_bytes = B * rows * (8 if args.path in ("split_fp16", "f64") else 4) + B * N * (8 if args.path == "f64" else 4)
-    nplanes = 7 if args.path == "split_fp16" else 1
-    prep_bytes = B * K * 4 + nplanes * B * Kp * 2 + B * 4 + (B * 8 if args.path == "split_fp16" else 0)
-    peak_tensor = peaks.get("bf16_tflops", 1899.1)
-    gemm_roof = {"kernel": "tc_gemm_kernel (Abel GEMM)", "bound": "tensor",
-                 "achieved": flops_useful / (gemm_ms / 1e3) / 1e12, "peak": peak_tensor, "unit": "TFLOP/s",
-                 "flops_per_launch": flops_useful, "executed_flops_per_launch": executed,
-                 "executed_tflops": executed / (gemm_ms / 1e3) / 1e12,
-                 "traffic": TRAFFIC.get(("abel_gemm", args.path, name)),
-                 "peak_source": "%s bf16_tflops (fp16 dense rate equals bf16)" % peak_src}
-    gemm_roof["frac"] = gemm_roof["achieved"] / peak_tensor
-    hbm = peaks.get("hbm_gbs", 6696.2)
-    fft_hbm = fft_bytes / (fft_ms / 1e3) / 1e9
-    if args.path in ("split_fp16", "f64"):
-        # double-float (or FP64) transform: bound by FP32 (FP64) arithmetic, see fft_fp32_ops
-        ops = fft_fp32_ops(M, N) * B
-        peak_alu = ALU_PEAK_TOPS["f64" if args.path == "f64" else "f32"]
-        fft_roof = {"kernel": "dct16_forward_kernel (FFT stage)", "bound": "alu",
-                    "achieved": ops / (fft_ms / 1e3) / 1e12, "peak": peak_alu, "unit": "Tops/s",
-                    "ops_per_launch": ops, "hbm_gbs": fft_hbm, "hbm_frac": fft_hbm / hbm,
-                    "traffic": TRAFFIC.get(("fft", args.path, name)),
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"}
-        fft_roof["frac"] = fft_roof["achieved"] / peak_alu
-    else:
-        fft_roof = {"kernel": "fft_forward_kernel (FFT stage)", "bound": "hbm", "achieved": fft_hbm, "peak": hbm,
-                    "unit": "GB/s", "frac": fft_hbm / hbm, "bytes_per_launch": fft_bytes,
-                    "traffic": TRAFFIC.get(("fft", args.path, name)), "peak_source": "%s hbm_gbs" % peak_src}
-    kernels = {"abel_gemm": gemm_ms, "fft": fft_ms, "input_split": prep_ms}
-    dom = max(kernels, key=kernels.get)
-    if dom == "fft":
-        roof = fft_roof
-    elif dom == "abel_gemm" and args.path in ("split_fp16", "bf16"):
-        roof = gemm_roof
-    else:
-        by = {"input_split": prep_bytes, "abel_gemm": B * K * 4 + rows * K * 4 + B * rows * 4}[dom]
-        achieved = by / (kernels[dom] / 1e3) / 1e9
-        roof = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                "frac": achieved / hbm, "traffic": None, "bytes_per_launch": by, "peak_source": "%s hbm_gbs" % peak_src}
-    stages = {
-        "input_split": {"ms": prep_ms, "bytes": prep_bytes,
-                        "gbs": prep_bytes / (prep_ms / 1e3) / 1e9 if prep_ms > 0 else None},
-        "abel_gemm": dict(gemm_roof, ms=gemm_ms) if args.path in ("split_fp16", "bf16") else
-                     {"ms": gemm_ms, "useful_tflops": flops_useful / (gemm_ms / 1e3) / 1e12},
-        "fft": dict(fft_roof, ms=fft_ms),
-    }
-
-    extras = {}
-    if not args.no_extras and args.path != "f64":
-        for p_name, st_n in (("f64", 3), ("f32", 5)):
-            if p_name == args.path:
-                continue
-            r = run_path(leg, torch, name, p_name, rank, st_n, 2, flush, sample_err=16)
-            ms = float(np.mean(r["step_ms"]))
-            extras[p_name + "_gpu_path"] = {"value": B * N / (ms / 1e3), "ms_per_step": ms,
-                                            "max_rel_err": relerr(r["c_sample"], ref)}
-            del r
-    if not args.no_extras and args.path == "split_fp16":
-        # the same map with L = R A multiplied out at plan time: split + one GEMM
-        r = run_path(leg, torch, name, "split_fp16", rank, 10, 3, flush, sample_err=16, flags=leg.FLAG_COLLAPSED)
-        st_ms = np.array(r["stage"]).mean(0)
-        ms = float(np.mean(r["step_ms"]))
-        cf_useful = 2.0 * B * N * K
-        cf_exec = 8 * 2.0 * B * N * Kp
-        extras["collapsed_split_fp16"] = {
-            "value": B * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "max_rel_err": relerr(r["c_sample"], ref),
-            "input_split_ms": float(st_ms[0]), "gemm_ms": float(st_ms[1]), "plan_build_s": r["plan_s"],
-            "gemm_useful_tflops": cf_useful / (st_ms[1] / 1e3) / 1e12,
-            "gemm_executed_tflops": cf_exec / (st_ms[1] / 1e3) / 1e12,
-            "gemm_executed_frac": cf_exec / (st_ms[1] / 1e3) / 1e12 / peak_tensor,
-            "launches_per_step": 2}
-        del r
-    if not args.no_extras:
-        extras.update(extra_workloads(leg, torch, flush, rank))
-    cpu = None
-    if not args.no_cpu_baseline:
-        cpu, _, _ = oracle_rate(name)
-    launches_per_step = {"split_fp16": 3, "bf16": 3, "f32": 2, "f64": 2}[args.path]
+    prep_ms, gemm_ms, fft_ms = res["_stage"]
+    roof = res["gemm_roofline"] if gemm_ms >= fft_ms else res["transform_roofline"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": DTYPE_STR[args.path], "data": "synthetic",
-        "config": {"workload": name, "B": B, "K": K, "N": N, "M": M, "Q": (K + 1) // 2, "path": args.path,
-                   "l2": "flushed (512 MiB write) before every timed step",
+        "config": {"workload": name, "B": B, "K": head.K, "N": N, "M": head.M, "Q": (head.K + 1) // 2,
+                   "path": args.path, "tile_width": head.tn,
+                   "l2": "flushed (512 MiB write) before every timed step; the operator planes (%.0f MB) also "
+                         "exceed L2" % (3 * (head.rows - 1) * head.Kp * 2 / 1e6),
                    "inputs": "random decaying Chebyshev series sampled at CL nodes, FP32, seeded"},
-        "max_rel_err": err, "err_sample": "16 functions vs FP64 oracle route 2",
-        "roofline": roof, "stages": stages, "plan_build_s": res["plan_s"],
-        "e2e": e2e, "clocks": clk, "gpu_launches": launches_per_step * args.steps,
-        "cpu_baseline": cpu,
+        "max_rel_err": res.get("max_rel_err"), "tolerance": 1e-6,
+        "err_sample": (res.get("err_sample", "") + " vs the FP64 oracle " + oracle_route_name(name)),
+        "roofline": roof, "stages_ms": res["stages_ms"],
+        "transform_roofline": res["transform_roofline"], "plan_build_s": head.plan_s.get(args.path),
+        "e2e": e2e, "clocks": res["_clk"], "gpu_launches": LAUNCHES[args.path] * args.steps,
     }
-    if extras:
-        line.update(extras)
-        if "f64_gpu_path" in extras:
-            line["speedup_vs_fp64_gpu_path"] = value / world / extras["f64_gpu_path"]["value"]
+    wl = {}
+    if not args.no_extras:
+        # precision sweep and the sine form on the headline workload
+        sweep = {args.path: {k: line[k] for k in ("value", "ms_per_step", "max_rel_err")}}
+        for p in ("f64", "f32", "bf16", "split_fp16"):
+            if p == args.path:
+                continue
+            r = head.run(p, flush, 3 if p == "f64" else 10, 2, peaks, peak_src)
+            sweep[p] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "max_rel_err": r.get("max_rel_err"),
+                        "stages_ms": r["stages_ms"]}
+        wl["precision_sweep_" + name] = sweep
+        line["speedup_vs_fp64_gpu_path"] = (value / world) / sweep["f64"]["value"]
+        if args.path in ("split_fp16", "f64", "f32", "bf16"):
+            r = head.run(args.path, flush, 20, 3, peaks, peak_src, transform=leg.TRANSFORM_SINE)
+            wl["sine_form_" + name] = strip(r)
+        del head
+        # the B=4096, K=1025 workload: split, plain FP32, FP64, collapsed
+        c2name = "cheb_b4096_k1025_n512_m2048"
+        c2 = Dense(leg, torch, c2name, rank, with_ref, extra=24)
+        sub = {}
+        sub["split_fp16"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src))
+        sub["split_fp16_sine_form"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src,
+                                                   transform=leg.TRANSFORM_SINE))
+        sub["f32"] = strip(c2.run("f32", flush, 20, 3, peaks, peak_src))
+        sub["f32_sine_form"] = strip(c2.run("f32", flush, 20, 3, peaks, peak_src, transform=leg.TRANSFORM_SINE))
+        sub["f64"] = strip(c2.run("f64", flush, 3, 1, peaks, peak_src))
+        sub["speedup_vs_fp64_gpu_path"] = sub["split_fp16"]["value"] / sub["f64"]["value"]
+        coll = leg.Plan(c2.N, c2.M, c2.K, 0, leg.SPLIT_FP16, flags=leg.FLAG_COLLAPSED)
+        cc = torch.empty((c2.B, c2.N), dtype=torch.float32, device="cuda")
+        ts, _ = time_steps(torch, lambda: coll.forward(c2.f32, cc), flush, 20, 3)
+        coll.status()
+        sub["collapsed_split_fp16"] = {"value": c2.B * c2.N / (np.mean(ts) / 1e3), "ms_per_step": float(np.mean(ts)),
+                                       "launches_per_step": 2}
+        if c2.ref is not None:
+            sub["collapsed_split_fp16"]["max_rel_err"] = relerr(
+                cc[torch.from_numpy(c2.sample).cuda()].double().cpu().numpy(), c2.ref)
+        wl[c2name] = sub
+        del c2, coll
+        wl["ragged_10000"] = ragged(leg, torch, flush, rank, peaks, peak_src, with_ref)
+        wl["cheb_b1024_k4097_n2048_m8192"] = differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref)
+        wl["genfn_plain_n64"] = plain_method(leg, torch)
+        from oracle import oracle as O
+        wl["table1_abs_x_3_2_plain_sine_form"] = table1_plain(leg, torch, O)
+        line["workloads"] = wl
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"], _, _ = oracle_rate(name)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()

@@ -27,6 +27,12 @@
  *    human-readable message for the last error of the calling thread is
  *    returned by leg_last_error().  Argument errors are reported before any
  *    work is enqueued.
+ *  - Fault injection (tests of the error paths): with the environment
+ *    variable LEG_FAULT_ALLOC = k (k >= 1), the k-th device allocation the
+ *    library attempts after the variable took that value fails on the host,
+ *    without allocating, and the call returns LEG_ERR_OOM having released
+ *    what it had allocated for that call (a plan's grown workspace stays with
+ *    the plan until it is destroyed).
  */
 #ifndef LEG_H
 #define LEG_H
@@ -96,6 +102,26 @@ typedef enum {
  * without this flag.
  */
 #define LEG_FLAG_COLLAPSED   2u
+/*
+ * LEG_FLAG_SINE_FORM: the plan's forward transform evaluates the half-range
+ * sine form of the coefficients (Eq. 2.13, with phi of Eq. 2.14; the paper
+ * derives it from the symmetry Eq. 2.12),
+ *     c_n = (2/pi)(n + 1/2) int_0^pi phi(y) sin((n + 1/2) y) dy,
+ *     phi(y) = int_{cos y}^1 f(x) / sqrt(2(x - cos y)) dx = 2 sin(y/2) g(y),
+ * by the trapezoid rule on y_j = 2 pi j / M, j = 0..M/2: a DST-III of length
+ * M/2 of phi, computed through one complex FFT of length M/4 (the factor
+ * 2 sin(y/2) merged into its pre-twiddle), instead of the real-even transform
+ * of the full period followed by a first difference (Eq. 2.4, Eq. 2.5).  Both
+ * are the same discrete linear map; results differ by rounding only.  Needs
+ * M >= 256 (LEG_ERR_UNSUPPORTED otherwise); not with LEG_FLAG_COLLAPSED.  The
+ * same choice is available on any plan through leg_plan_set_transform.
+ */
+#define LEG_FLAG_SINE_FORM   4u
+
+/* Forward transform kernels (leg_plan_set_transform); the same map, rounding differs. */
+#define LEG_TRANSFORM_REG      0  /* register-tiled real-even transform (M >= 256; FP32 plans: Stockham) */
+#define LEG_TRANSFORM_STOCKHAM 1  /* shared-memory Stockham real-even transform                     */
+#define LEG_TRANSFORM_SINE     2  /* register-tiled half-range sine form, Eq. 2.13 (M >= 256)        */
 
 typedef struct leg_plan *leg_plan_t;
 
@@ -182,12 +208,15 @@ LEG_API int leg_backward(leg_plan_t plan, const void *dc, void *df, int B, cudaS
  * then the same FFT.  FP64 throughout; uses N, M, Q of the plan (any dtype).
  *   family  LEG_FAMILY_GENFN: f(x) = (1 - 2 x t + t^2)^(-1/2)  (Eq. 2.2),
  *                            params[b] = t, |t| < 1;
- *           LEG_FAMILY_EXP:   f(x) = exp(a x), params[b] = a.
+ *           LEG_FAMILY_EXP:   f(x) = exp(a x), params[b] = a;
+ *           LEG_FAMILY_ABSPOW: f(x) = |x|^alpha, params[b] = alpha > 0.
  *   params  device, B doubles.   c  device, B x N doubles.
  */
 #define LEG_FAMILY_GENFN 0
 #define LEG_FAMILY_EXP   1
 #define LEG_FAMILY_CHEB  2   /* leg_sample_cl, leg_plain_forward_cheb: sum_m coef_m T_m(x) */
+#define LEG_FAMILY_ABSPOW 3  /* leg_plain_forward: f(x) = |x|^alpha, params[b] = alpha > 0
+                                (Table 1's test function for alpha = 3/2, Eq. 2.15)       */
 LEG_API int leg_plain_forward(leg_plan_t plan, int family, const double *params, int B,
                       double *c, cudaStream_t stream);
 
@@ -206,27 +235,75 @@ LEG_API int leg_plain_forward_cheb(leg_plan_t plan, const double *coef, int Kc, 
 /*
  * Ragged batches (functions of different sizes, grouped in size buckets).
  *
+ * leg_forward_ragged -- Theorem 1 (Eq. 2.4, Eq. 2.5) for every function of a
+ * ragged batch in one call:
+ *   plans[0..nplans-1]  bucket plans (LEG_SPLIT_FP16, current device, without
+ *                       LEG_FLAG_COLLAPSED); 1 <= nplans <= 64;
+ *   count               functions in the batch (0 is a no-op);
+ *   plan_idx[i]         bucket of function i (0..nplans-1);
+ *   n_out[i]            coefficients kept for function i, 1..N of its plan;
+ *   in_off[i]           offset (in floats) of its K samples in f_packed;
+ *   out_off[i]          offset (in floats) of its n_out[i] coefficients in
+ *                       c_packed;
+ *   f_packed, c_packed  device, FP32.
+ * The four per-function arrays are device arrays (host pointers also work on
+ * unified-addressing systems).  They are read back once per call, ordered
+ * after the work already on `stream` (count x 24 bytes, one host
+ * synchronisation with the stream); the batch built from them (workspaces,
+ * the grouped-GEMM tile list, a CUDA graph) is kept in a cache of the four
+ * most recently used batches, keyed by the device, the plans and the arrays'
+ * contents, and replayed by later calls with the same key.  Destroying a plan
+ * drops the cached batches that use it.  Calls from several host threads
+ * share the cache: their launches are enqueued one at a time, and calls whose
+ * work overlaps on the GPU through the same cached batch race on its
+ * workspace.  Not while `stream` is being captured (LEG_ERR_UNSUPPORTED): the
+ * handle-based form below has no host synchronisation and joins a caller's
+ * capture.  Errors: as leg_ragged_create, and LEG_ERR_INVALID_ARG for null
+ * arrays.
+ */
+LEG_API int leg_forward_ragged(const leg_plan_t *plans, int nplans, int count, const int *plan_idx,
+                               const int *n_out, const long long *in_off, const long long *out_off,
+                               const float *f_packed, float *c_packed, cudaStream_t stream);
+
+/*
+ * The same computation with an explicit batch handle.
+ *
  * leg_ragged_create -- prepare the computation of `count` functions over the
  * bucket plans plans[0..nplans-1] (all LEG_SPLIT_FP16, current device).
- * Host arrays, copied:
- *   plan_idx[i]  bucket of function i (0..nplans-1);
- *   n_out[i]     coefficients kept for function i, 1..N of its plan;
- *   in_off[i]    offset (in floats) of its K samples in the packed input;
- *   out_off[i]   offset (in floats) of its n_out[i] coefficients in the
- *                packed output.
- * Allocates the per-bucket workspaces, a private stream and three streams
- * for the concurrent transforms; synchronises.
- * The plans must outlive the batch.
+ * Host arrays, copied (meanings as for leg_forward_ragged).  Allocates the
+ * per-bucket workspaces, a private stream and three streams for the
+ * concurrent transforms; synchronises.  The tile width of the grouped GEMM is
+ * the one stored in the tuning cache (LEG_TUNE_CACHE) for this batch's
+ * buckets by leg_ragged_autotune, else the library's cost model.  The plans
+ * must outlive the batch.
  *
- * leg_forward_ragged -- Theorem 1 (Eq. 2.4, Eq. 2.5) for every function of
- * the batch: one input-split launch over all functions, ONE persistent
- * tcgen05 launch over the Abel-GEMM tiles of all buckets, one transform
- * launch per bucket writing the packed output (the transforms of the buckets
- * run concurrently on the batch's internal streams).  The first call runs the
- * sequence directly; later calls replay it as a CUDA graph (captured again
- * when f_packed or c_packed change).  When `stream` is itself being captured,
- * the launches join the caller's graph instead.  Ordered after prior work on
- * `stream`, and later work on `stream` waits for it.  Device pointers.
+ * leg_ragged_forward -- one input-split launch over all functions, ONE
+ * persistent tcgen05 launch over the Abel-GEMM tiles of all buckets, one
+ * transform launch per bucket writing the packed output (the transforms of
+ * the buckets run concurrently on the batch's internal streams; each uses its
+ * plan's transform kernel, see leg_plan_set_transform).  The first call runs
+ * the sequence directly; later calls replay it as a CUDA graph (captured
+ * again when f_packed, c_packed or the tile width change).  When `stream` is
+ * itself being captured, the launches join the caller's graph instead.
+ * Ordered after prior work on `stream`, and later work on `stream` waits for
+ * it.  Device pointers; no host synchronisation.
+ *
+ * leg_ragged_forward_profiled -- the same launches run directly with CUDA
+ * events between the stages; blocks the host until they complete and writes
+ * ms[0] input split, ms[1] grouped Abel GEMM, ms[2] transforms (all buckets,
+ * concurrent).  ms: host array of 3 floats.
+ *
+ * leg_ragged_set_tile -- width of the grouped GEMM's tiles: a multiple of 16
+ * in 16..128, or 0 for the cost model's choice; synchronises the batch's
+ * stream.  Results do not depend on it.  leg_ragged_tile_info -- the current
+ * width and the number of pair tiles of the grouped launch (either may be NULL).
+ *
+ * leg_ragged_autotune -- time the grouped GEMM at the model's tile width and
+ * at 128, 112, ..., 64 on the caller's data (each candidate once untimed and
+ * three times timed, leg_ragged_forward_profiled), keep the fastest, and,
+ * with LEG_TUNE_CACHE naming a file, store it there keyed by the device and
+ * every bucket's (N, M, K, Q, functions); a stored choice is taken without
+ * timing.  c_packed is overwritten.  *tn (may be NULL): the chosen width.
  *
  * leg_ragged_status -- as leg_plan_status, for the batch's kernels.
  */
@@ -234,8 +311,13 @@ typedef struct leg_ragged *leg_ragged_t;
 LEG_API int leg_ragged_create(leg_ragged_t *out, const leg_plan_t *plans, int nplans, int count,
                               const int *plan_idx, const int *n_out, const long long *in_off,
                               const long long *out_off);
-LEG_API int leg_forward_ragged(leg_ragged_t batch, const float *f_packed, float *c_packed,
-                               cudaStream_t stream);
+LEG_API int leg_ragged_forward(leg_ragged_t batch, const float *f_packed, float *c_packed, cudaStream_t stream);
+LEG_API int leg_ragged_forward_profiled(leg_ragged_t batch, const float *f_packed, float *c_packed,
+                                        cudaStream_t stream, float *ms);
+LEG_API int leg_ragged_set_tile(leg_ragged_t batch, int tn);
+LEG_API int leg_ragged_tile_info(leg_ragged_t batch, int *tn, int *tiles);
+LEG_API int leg_ragged_autotune(leg_ragged_t batch, const float *f_packed, float *c_packed, cudaStream_t stream,
+                                int *tn);
 LEG_API int leg_ragged_status(leg_ragged_t batch, int reset);
 LEG_API int leg_ragged_destroy(leg_ragged_t batch);
 
@@ -281,6 +363,19 @@ LEG_API int leg_plan_set_wait_limit(leg_plan_t plan, long long cycles);
 LEG_API int leg_plan_set_tile(leg_plan_t plan, int tn);
 
 /*
+ * leg_plan_set_transform -- the kernel of the plan's forward transform stage:
+ * LEG_TRANSFORM_REG (the default), LEG_TRANSFORM_STOCKHAM or
+ * LEG_TRANSFORM_SINE (the sine form of Eq. 2.13, see LEG_FLAG_SINE_FORM;
+ * M >= 256, else LEG_ERR_UNSUPPORTED).  All three compute the same linear
+ * map; results differ by rounding.  The plain method (leg_plain_forward*) and
+ * ragged batches use the plan's choice too; leg_backward always applies the
+ * real-even adjoint (the transpose of that same map).
+ * leg_plan_get_transform -- the current choice.
+ */
+LEG_API int leg_plan_set_transform(leg_plan_t plan, int variant);
+LEG_API int leg_plan_get_transform(leg_plan_t plan, int *variant);
+
+/*
  * leg_plan_tile_info -- the tile of the forward GEMM for a batch of B
  * functions: *tn functions per pair tile, *pairs CTA pairs resident at once
  * on the current device, *tiles pair tiles of the launch.  LEG_SPLIT_FP16
@@ -322,7 +417,8 @@ LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cu
  * rounded up to 32, Mr = M/2+1 rounded up to 32) is rejected with
  * LEG_ERR_INVALID_ARG and a message stating the sizes.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
+ * device current, and so does the first call after the device's context
+ * changed (cudaDeviceReset); make those calls before any stream capture.  All calls
  * share the array and it keeps the last call's contents: calls whose work
  * overlaps on the GPU race on it, so serialise them.
  */
@@ -353,6 +449,17 @@ LEG_API int leg_forward_noalloc(leg_plan_t plan, const float *f, float *c, int B
  * internal streams; growing them synchronises the device.
  */
 LEG_API int leg_forward_host(leg_plan_t plan, const void *f_host, void *c_host, int B, cudaStream_t stream);
+
+/*
+ * leg_memory_info -- device memory the library holds at this moment for the
+ * objects it created (plans and their workspaces, ragged batches, the
+ * host-buffer path's copies, cached one-call batches): the number of live
+ * allocations and their total bytes, over all devices.  The static scratch of
+ * leg_forward_noalloc is not counted.  Either output may be NULL.  A library
+ * diagnostic with no counterpart in the paper; the error-path tests use it to
+ * show that failed calls release what they took.
+ */
+LEG_API int leg_memory_info(long long *allocations, long long *bytes);
 
 /* Message for the most recent failing call on this host thread ("" if none). */
 LEG_API const char *leg_last_error(void);

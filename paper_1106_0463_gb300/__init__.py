@@ -21,15 +21,20 @@ import re
 import torch
 
 __all__ = [
-    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FLAG_COLLAPSED", "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB",
-    "Ragged", "sample_cl",
+    "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FLAG_COLLAPSED", "FLAG_SINE_FORM",
+    "TRANSFORM_REG", "TRANSFORM_STOCKHAM", "TRANSFORM_SINE",
+    "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB", "FAMILY_ABSPOW",
+    "Ragged", "forward_ragged", "sample_cl",
     "LegError", "Plan", "LegendreFn", "legendre", "library_path", "declared_symbols", "load_library",
+    "memory_info",
 ]
 
 F64, F32, BF16, SPLIT_FP16 = 0, 1, 2, 3
 FLAG_TAU_LITERAL = 1
 FLAG_COLLAPSED = 2    # c = L f with L = R A multiplied out at plan time (one GEMM, no transform)
-FAMILY_GENFN, FAMILY_EXP, FAMILY_CHEB = 0, 1, 2
+FLAG_SINE_FORM = 4    # forward transform by the half-range sine form (Eq. 2.13)
+TRANSFORM_REG, TRANSFORM_STOCKHAM, TRANSFORM_SINE = 0, 1, 2
+FAMILY_GENFN, FAMILY_EXP, FAMILY_CHEB, FAMILY_ABSPOW = 0, 1, 2, 3
 _ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -76,13 +81,21 @@ def _load():
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
+        "leg_plan_set_transform": ([vp, i], i),
+        "leg_plan_get_transform": ([vp, ctypes.POINTER(i)], i),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_tile_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_ragged_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i, i, vp, vp, vp, vp], i),
-        "leg_forward_ragged": ([vp, vp, vp, vp], i),
+        "leg_ragged_forward": ([vp, vp, vp, vp], i),
+        "leg_ragged_forward_profiled": ([vp, vp, vp, vp, ctypes.POINTER(ctypes.c_float)], i),
+        "leg_ragged_set_tile": ([vp, i], i),
+        "leg_ragged_tile_info": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
+        "leg_ragged_autotune": ([vp, vp, vp, vp, ctypes.POINTER(i)], i),
+        "leg_forward_ragged": ([ctypes.POINTER(vp), i, i, vp, vp, vp, vp, vp, vp, vp], i),
         "leg_ragged_status": ([vp, i], i),
         "leg_ragged_destroy": ([vp], i),
         "leg_sample_cl": ([i, vp, vp, vp, vp, vp, vp, vp, vp], i),
+        "leg_memory_info": ([ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)], i),
         "leg_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
@@ -109,6 +122,13 @@ _lib = _LazyLib()
 def load_library():
     """Load libleg.so now (raises ImportError when it has not been built)."""
     return _lib.leg_last_error
+
+
+def memory_info() -> tuple[int, int]:
+    """(live device allocations, bytes) the library holds (leg_memory_info)."""
+    n, b = ctypes.c_longlong(), ctypes.c_longlong()
+    _check(_lib.leg_memory_info(ctypes.byref(n), ctypes.byref(b)))
+    return n.value, b.value
 
 
 def _check(rc: int):
@@ -200,6 +220,17 @@ class Plan:
     def set_tile(self, tn: int):
         """Functions per CTA-pair tile of the tensor-core GEMM (0 = automatic)."""
         _check(_lib.leg_plan_set_tile(self._h, int(tn)))
+
+    def set_transform(self, variant: int):
+        """Kernel of the forward transform stage: TRANSFORM_REG, TRANSFORM_STOCKHAM
+        or TRANSFORM_SINE (leg_plan_set_transform); same map, rounding differs."""
+        _check(_lib.leg_plan_set_transform(self._h, int(variant)))
+
+    @property
+    def transform(self) -> int:
+        v = ctypes.c_int()
+        _check(_lib.leg_plan_get_transform(self._h, ctypes.byref(v)))
+        return v.value
 
     def autotune(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> dict:
         """leg_plan_autotune: time the GEMM tile widths and the transform
@@ -323,7 +354,7 @@ def legendre(f: torch.Tensor, plan: Plan) -> torch.Tensor:
 
 
 class Ragged:
-    """A ragged batch over size-bucket plans (leg_ragged_create / leg_forward_ragged).
+    """A ragged batch over size-bucket plans (leg_ragged_create / leg_ragged_forward).
 
     plans: list of SPLIT_FP16 Plans; plan_idx, n_out, in_off, out_off: per
     function (host sequences).  forward() reads the packed FP32 samples and
@@ -346,15 +377,41 @@ class Ragged:
         self.n_in = int((io + np.array([p.K for p in self.plans])[pi]).max()) if self.count else 0
         self.n_out = int((oo + no).max()) if self.count else 0
 
-    def forward(self, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None) -> torch.Tensor:
+    def _io(self, f_packed, c_packed):
         for t, nm, n in ((f_packed, "f_packed", self.n_in), (c_packed, "c_packed", self.n_out)):
             if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
                 raise ValueError("%s must be a contiguous float32 CUDA tensor" % nm)
             if t.numel() < n:
                 raise ValueError("%s needs at least %d elements" % (nm, n))
-        _check(_lib.leg_forward_ragged(self._h, ctypes.c_void_p(f_packed.data_ptr()),
-                                       ctypes.c_void_p(c_packed.data_ptr()), _stream(stream)))
+        return ctypes.c_void_p(f_packed.data_ptr()), ctypes.c_void_p(c_packed.data_ptr())
+
+    def forward(self, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None) -> torch.Tensor:
+        pf, pc = self._io(f_packed, c_packed)
+        _check(_lib.leg_ragged_forward(self._h, pf, pc, _stream(stream)))
         return c_packed
+
+    def forward_profiled(self, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None):
+        """Stage times in ms (split, grouped GEMM, transforms); synchronises."""
+        pf, pc = self._io(f_packed, c_packed)
+        ms = (ctypes.c_float * 3)()
+        _check(_lib.leg_ragged_forward_profiled(self._h, pf, pc, _stream(stream), ms))
+        return tuple(float(v) for v in ms)
+
+    def set_tile(self, tn: int):
+        """Tile width of the grouped GEMM (0 = the cost model's choice)."""
+        _check(_lib.leg_ragged_set_tile(self._h, int(tn)))
+
+    def tile_info(self) -> dict:
+        tn, tiles = ctypes.c_int(), ctypes.c_int()
+        _check(_lib.leg_ragged_tile_info(self._h, ctypes.byref(tn), ctypes.byref(tiles)))
+        return {"tn": tn.value, "tiles": tiles.value}
+
+    def autotune(self, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None) -> int:
+        """leg_ragged_autotune: time the grouped GEMM's tile widths on this data, keep the fastest."""
+        pf, pc = self._io(f_packed, c_packed)
+        tn = ctypes.c_int()
+        _check(_lib.leg_ragged_autotune(self._h, pf, pc, _stream(stream), ctypes.byref(tn)))
+        return tn.value
 
     def status(self, reset: bool = True):
         _check(_lib.leg_ragged_status(self._h, int(bool(reset))))
@@ -369,6 +426,26 @@ class Ragged:
             self.close()
         except Exception:
             pass
+
+
+def forward_ragged(plans, plan_idx: torch.Tensor, n_out: torch.Tensor, in_off: torch.Tensor,
+                   out_off: torch.Tensor, f_packed: torch.Tensor, c_packed: torch.Tensor, stream=None) -> torch.Tensor:
+    """leg_forward_ragged: a ragged batch in one call, the per-function arrays
+    given as CUDA tensors (plan_idx, n_out int32; in_off, out_off int64).  The
+    library reads the arrays back and caches the batch built from them."""
+    count = plan_idx.numel()
+    for t, nm, dt in ((plan_idx, "plan_idx", torch.int32), (n_out, "n_out", torch.int32),
+                      (in_off, "in_off", torch.int64), (out_off, "out_off", torch.int64)):
+        _dev_tensor(t, dt, (count,), nm)
+    for t, nm in ((f_packed, "f_packed"), (c_packed, "c_packed")):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+            raise ValueError("%s must be a contiguous float32 CUDA tensor" % nm)
+    plans = list(plans)
+    hp = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())
+    _check(_lib.leg_forward_ragged(hp, len(plans), count, ptr(plan_idx), ptr(n_out), ptr(in_off), ptr(out_off),
+                                   ptr(f_packed), ptr(c_packed), _stream(stream)))
+    return c_packed
 
 
 def sample_cl(family, param, K, in_off, f_packed, coef=None, coef_off=None, stream=None):

@@ -2,8 +2,10 @@
 // The operations and their citations are documented in include/leg.h.
 #include <stdlib.h>
 
+#include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 
 #include "leg_internal.cuh"
 
@@ -14,12 +16,12 @@ bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
 
 void free_workspace(leg_plan *p)
 {
-    cudaFree(p->G);
-    cudaFree(p->Gbar);
-    cudaFree(p->Fh);
+    leg_dev_free(p->G);
+    leg_dev_free(p->Gbar);
+    leg_dev_free(p->Fh);
     p->Fh = nullptr;
-    cudaFree(p->Fbf);
-    cudaFree(p->fexp);
+    leg_dev_free(p->Fbf);
+    leg_dev_free(p->fexp);
     p->G = p->Gbar = nullptr;
     p->Fbf = nullptr;
     p->fexp = nullptr;
@@ -29,24 +31,25 @@ void free_workspace(leg_plan *p)
 void free_plan(leg_plan *p)
 {
     if (!p) return;
+    leg_ragged_forget_plan(p);
     if (p->fwd_exec) cudaGraphExecDestroy(p->fwd_exec);
     if (p->cap) cudaStreamDestroy(p->cap);
     leg_host_free(p);
     free_workspace(p);
-    cudaFree(p->omt2);
-    cudaFree(p->wq);
-    cudaFree(p->A64);
-    cudaFree(p->L64);
-    cudaFree(p->A32);
-    cudaFree(p->Ah[0]);    // the three planes share one allocation
-    cudaFree(p->AhT[0]);
-    cudaFree(p->Abf);
-    cudaFree(p->rowexp);
-    cudaFree(p->colexp);
-    cudaFree(p->status);
-    cudaFree(p->tw64);
-    cudaFree(p->tw32);
-    cudaFree(p->twdf);
+    leg_dev_free(p->omt2);
+    leg_dev_free(p->wq);
+    leg_dev_free(p->A64);
+    leg_dev_free(p->L64);
+    leg_dev_free(p->A32);
+    leg_dev_free(p->Ah[0]);    // the three planes share one allocation
+    leg_dev_free(p->AhT[0]);
+    leg_dev_free(p->Abf);
+    leg_dev_free(p->rowexp);
+    leg_dev_free(p->colexp);
+    leg_dev_free(p->status);
+    leg_dev_free(p->tw64);
+    leg_dev_free(p->tw32);
+    leg_dev_free(p->twdf);
     delete p;
 }
 
@@ -71,16 +74,16 @@ int ensure_workspace(leg_plan *p, int B)
         p->ldg = 0;   // one GEMM straight into c / df: no G
     } else {
         p->ldg = (p->dtype == LEG_SPLIT_FP16) ? bwdKp : rowsKp;
-        LEG_CUDA_TRY(cudaMalloc(&p->G, eb * Bz * p->ldg));
-        LEG_CUDA_TRY(cudaMalloc(&p->Gbar, eb * Bz * p->ldg));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->G, eb * Bz * p->ldg));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->Gbar, eb * Bz * p->ldg));
     }
     if (p->dtype == LEG_SPLIT_FP16) {
         // input planes serve both directions: B x Kp (forward) or B x bwdKp (adjoint)
         p->ldf = (p->Kp > bwdKp) ? p->Kp : bwdKp;
-        LEG_CUDA_TRY(cudaMalloc(&p->Fh, sizeof(__half) * LEG_SPLIT_NF * Bz * p->ldf));
-        LEG_CUDA_TRY(cudaMalloc(&p->fexp, sizeof(int) * Bz));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->Fh, sizeof(__half) * LEG_SPLIT_NF * Bz * p->ldf));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->fexp, sizeof(int) * Bz));
     } else if (p->dtype == LEG_BF16) {
-        LEG_CUDA_TRY(cudaMalloc(&p->Fbf, sizeof(__nv_bfloat16) * Bz * p->Kp));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->Fbf, sizeof(__nv_bfloat16) * Bz * p->Kp));
     }
     p->ws_B = B;
     return LEG_OK;
@@ -96,6 +99,91 @@ int check_plan(leg_plan *p)
     return LEG_OK;
 }
 }  // namespace
+
+namespace {
+std::mutex g_alloc_mutex;
+std::unordered_map<void *, size_t> g_live;   // live device allocations of the library and their sizes
+long long g_live_bytes = 0;
+std::string g_fault_setting;   // value of LEG_FAULT_ALLOC the count below refers to
+long long g_fault_count = 0;   // allocations since LEG_FAULT_ALLOC took that value
+
+// true when this allocation is the one LEG_FAULT_ALLOC asks to fail
+bool fault_injected()
+{
+    const char *env = getenv("LEG_FAULT_ALLOC");
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    const std::string v = env ? env : "";
+    if (v != g_fault_setting) {
+        g_fault_setting = v;
+        g_fault_count = 0;
+    }
+    const long long k = env ? atoll(env) : 0;
+    if (k < 1) return false;
+    return ++g_fault_count == k;
+}
+}  // namespace
+
+namespace {
+void track(void *ptr, size_t bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    g_live[ptr] = bytes;
+    g_live_bytes += (long long)bytes;
+}
+
+void untrack(void *ptr)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    auto it = g_live.find(ptr);
+    if (it == g_live.end()) return;
+    g_live_bytes -= (long long)it->second;
+    g_live.erase(it);
+}
+}  // namespace
+
+cudaError_t leg_dev_malloc_bytes(void **ptr, size_t bytes)
+{
+    if (fault_injected()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMalloc(ptr, bytes);
+    if (e == cudaSuccess) track(*ptr, bytes);
+    return e;
+}
+
+cudaError_t leg_dev_malloc_async_bytes(void **ptr, size_t bytes, cudaStream_t st)
+{
+    if (fault_injected()) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocAsync(ptr, bytes, st);
+    if (e == cudaSuccess) track(*ptr, bytes);
+    return e;
+}
+
+cudaError_t leg_dev_free(void *ptr)
+{
+    if (!ptr) return cudaSuccess;
+    untrack(ptr);
+    return cudaFree(ptr);
+}
+
+cudaError_t leg_dev_free_async(void *ptr, cudaStream_t st)
+{
+    if (!ptr) return cudaSuccess;
+    untrack(ptr);
+    return cudaFreeAsync(ptr, st);
+}
+
+extern "C" int leg_memory_info(long long *allocations, long long *bytes)
+{
+    std::lock_guard<std::mutex> lock(g_alloc_mutex);
+    if (allocations) *allocations = (long long)g_live.size();
+    if (bytes) *bytes = g_live_bytes;
+    return LEG_OK;
+}
 
 int leg_set_error(int code, const std::string &msg)
 {
@@ -119,8 +207,12 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
         return leg_set_error(LEG_ERR_INVALID_ARG, "Q must be in [0, 16384]");
     if (dtype < LEG_F64 || dtype > LEG_SPLIT_FP16)
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown dtype");
-    if (flags & ~(LEG_FLAG_TAU_LITERAL | LEG_FLAG_COLLAPSED))
+    if (flags & ~(LEG_FLAG_TAU_LITERAL | LEG_FLAG_COLLAPSED | LEG_FLAG_SINE_FORM))
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown flag");
+    if ((flags & LEG_FLAG_SINE_FORM) && (flags & LEG_FLAG_COLLAPSED))
+        return leg_set_error(LEG_ERR_INVALID_ARG, "LEG_FLAG_SINE_FORM selects a transform; collapsed plans have none");
+    if ((flags & LEG_FLAG_SINE_FORM) && M < LEG_TRANSFORM_MIN_M_REG)
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "LEG_FLAG_SINE_FORM needs M >= 256");
 
     leg_plan *p = new (std::nothrow) leg_plan();
     if (!p) return leg_set_error(LEG_ERR_OOM, "host allocation of the plan failed");
@@ -134,6 +226,7 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
     p->L = M / 2;
     p->rows = M / 2 + 1;
     p->Kp = leg_round_up(K, LEG_KPAD);
+    if (flags & LEG_FLAG_SINE_FORM) p->fft_variant = LEG_TRANSFORM_SINE;
     int rc = LEG_OK;
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
@@ -143,7 +236,7 @@ extern "C" int leg_plan_create_ex(leg_plan_t *out, int N, int M, int K, int Q, i
         long long v = atoll(env);
         if (v > 0) p->wait_limit = v;
     }
-    if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
+    if (leg_dev_malloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess) {
         free_plan(p);
         return leg_set_error(LEG_ERR_OOM, "status word allocation failed");
     }
@@ -181,15 +274,16 @@ extern "C" int leg_plan_create_like(leg_plan_t *out, leg_plan_t src, int dtype)
     p->Kp = src->Kp;
     p->device = src->device;
     p->wait_limit = src->wait_limit;
+    if (p->flags & LEG_FLAG_SINE_FORM) p->fft_variant = LEG_TRANSFORM_SINE;
     auto fail = [&](int code, const char *what) {
         free_plan(p);
         return leg_set_error(code, what);
     };
-    if (cudaMalloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
+    if (leg_dev_malloc(&p->status, sizeof(int)) != cudaSuccess || cudaMemset(p->status, 0, sizeof(int)) != cudaSuccess)
         return fail(LEG_ERR_OOM, "status word allocation failed");
-    if (cudaMalloc(&p->omt2, sizeof(double) * p->Q) != cudaSuccess ||
-        cudaMalloc(&p->wq, sizeof(double) * p->Q) != cudaSuccess ||
-        cudaMalloc(&p->A64, sizeof(double) * (size_t)p->rows * p->K) != cudaSuccess)
+    if (leg_dev_malloc(&p->omt2, sizeof(double) * p->Q) != cudaSuccess ||
+        leg_dev_malloc(&p->wq, sizeof(double) * p->Q) != cudaSuccess ||
+        leg_dev_malloc(&p->A64, sizeof(double) * (size_t)p->rows * p->K) != cudaSuccess)
         return fail(LEG_ERR_OOM, "operator allocation failed");
     if (cudaMemcpy(p->omt2, src->omt2, sizeof(double) * p->Q, cudaMemcpyDeviceToDevice) != cudaSuccess ||
         cudaMemcpy(p->wq, src->wq, sizeof(double) * p->Q, cudaMemcpyDeviceToDevice) != cudaSuccess ||
@@ -439,11 +533,11 @@ int plain_run(leg_plan *p, int B, double *c, cudaStream_t st, Fill fill)
         G = static_cast<double *>(p->G);
         ldg = p->ldg;
     } else {
-        LEG_CUDA_TRY(cudaMallocAsync(reinterpret_cast<void **>(&G), sizeof(double) * (size_t)B * ldg, st));
+        LEG_CUDA_TRY(leg_dev_malloc_async_bytes(reinterpret_cast<void **>(&G), sizeof(double) * (size_t)B * ldg, st));
     }
     rc = fill(G, ldg);
     if (!rc) rc = leg_fft_forward_f64(p, G, ldg, c, B, st);
-    if (G != p->G) cudaFreeAsync(G, st);
+    if (G != p->G) leg_dev_free_async(G, st);
     return rc;
 }
 
@@ -452,7 +546,7 @@ extern "C" int leg_plain_forward(leg_plan_t p, int family, const double *params,
 {
     int rc = check_plan(p);
     if (rc) return rc;
-    if (family != LEG_FAMILY_GENFN && family != LEG_FAMILY_EXP)
+    if (family != LEG_FAMILY_GENFN && family != LEG_FAMILY_EXP && family != LEG_FAMILY_ABSPOW)
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown family");
     if (B < 0 || B > 65535) return leg_set_error(LEG_ERR_INVALID_ARG, "B must be in [0, 65535]");
     if (B == 0) return LEG_OK;
@@ -499,6 +593,24 @@ extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
         return leg_set_error(LEG_ERR_INVALID_ARG, "tile width must be 0 or a multiple of 16 in 16.." +
                                                       std::to_string(maxtn) + " for this plan");
     p->tn = tn;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_set_transform(leg_plan_t p, int variant)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (variant < LEG_TRANSFORM_REG || variant > LEG_TRANSFORM_SINE)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "unknown transform variant");
+    if (variant == LEG_TRANSFORM_SINE && p->M < LEG_TRANSFORM_MIN_M_REG)
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "the sine-form transform needs M >= 256");
+    p->fft_variant = variant;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_get_transform(leg_plan_t p, int *variant)
+{
+    if (!p || !variant) return leg_set_error(LEG_ERR_INVALID_ARG, "null plan or variant");
+    *variant = p->fft_variant;
     return LEG_OK;
 }
 

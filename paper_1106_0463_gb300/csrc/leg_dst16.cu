@@ -1,0 +1,166 @@
+// Register-tiled sine-form transform for the FFT stage (FP64, double-float, FP32).
+//
+// The half-range sine form of the coefficients (arXiv:1106.0463, Eq. 2.13
+// with phi of Eq. 2.14; the paper obtains it from the symmetry Eq. 2.12):
+//   c_n = (2/pi)(n + 1/2) int_0^pi phi(y) sin((n + 1/2) y) dy,
+//   phi(y) = int_{cos y}^1 f(x) / sqrt(2(x - cos y)) dx = 2 sin(y/2) g(y),
+// with g the row of G that the Abel GEMM (or the plain method) delivers on
+// y_j = pi j / L, j = 0..L (L = M/2).  The trapezoid rule on [0, pi] gives
+//   c_n = ((2n+1) / L) sum''_{j=0..L} phi_j sin((n + 1/2) pi j / L)
+// (end points at half weight; phi_0 = 0), a DST-III of length L.
+//
+// Fast evaluation.  With m = L - j, sin((n + 1/2) pi (L - m)/L) =
+// (-1)^n cos(pi m (2n+1) / (2L)), so the sum is (-1)^n times a DCT-III of
+// v_m = phi_{L-m} (v_0 = phi_L enters at half weight, v_L = phi_0 = 0).  A
+// DCT-III of length L is the real output z of the length-L inverse DFT of
+// the Hermitian sequence W_k = e^{i pi k / M} (v_k - i v_{L-k}), read as
+//   DCT-III_{2p} = z_p / 2,   DCT-III_{2p+1} = z_{L-1-p} / 2.
+// The factor 2 sin(y/2) of phi merges into the pre-twiddle: with
+// theta = pi k / M, v_k = 2 cos(theta) g_{L-k} and v_{L-k} = 2 sin(theta) g_k,
+//   W_k = (g_k + g_{L-k}) + e^{2 pi i k / M} (g_{L-k} - g_k),   W_0 = 2 g_L,
+// so only the M-th roots of unity of the plan's twiddle table appear.  The
+// real-output DFT of length L is one complex FFT of length H = L/2:
+//   Y_k = (W_k + conj W_{H-k}) + i e^{2 pi i k / L} (W_k - conj W_{H-k}),
+//   zeta = FFT_H(Y) (positive exponent),  zeta_m = z_{2m} + i z_{2m+1},
+// and finally c_n = (-1)^n (2n+1) z_{i(n)} / M, i(2p) = p, i(2p+1) = L-1-p.
+//
+// Against the real-even route of leg_dct16.cu (the same discrete map, Theorem 1
+// with the twist as a first difference): the pre-twiddle replaces the fold,
+// and there is no recombination after the FFT and no prefix scan, so the
+// outputs need no first difference of two large sums.
+#include "leg_rtile.cuh"
+
+namespace {
+
+// zeta = FFT_H(Y) of the row delivered by load(j), j = 0..L (the caller's
+// element type converted to the arithmetic type), left in buf[D::pc(m)].
+template <class R, int LOG2H, class Load>
+__device__ __forceinline__ void dst16(CxT<R> *buf, int t, const typename Ar<R>::TW *tw, Load load)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
+    CxT<R> v[E];
+    // W_k of the merged pre-twiddle (k = 0..H)
+    auto wk = [&](int k) -> CxT<R> {
+        if (k == 0) return {F::pow2(load(L), 1), F::zero()};
+        const T_ a = load(k), b = load(L - k);
+        T_ c, s;
+        twid(tw, k, c, s);   // e^{2 pi i k / M}
+        const T_ d = F::sub(b, a);
+        return {F::add(F::add(a, b), F::mul(c, d)), F::mul(s, d)};
+    };
+    // 1. Y_k for k = t + b T
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+        const int k = t + b * T;
+        const CxT<R> w = wk(k), u = wk(H - k);
+        // W_k + conj W_{H-k} and W_k - conj W_{H-k}
+        const T_ pre = F::add(w.re, u.re), pim = F::sub(w.im, u.im);
+        const T_ dre = F::sub(w.re, u.re), dim = F::add(w.im, u.im);
+        T_ c, s;
+        twid(tw, 2 * k, c, s);   // e^{2 pi i k / L}
+        // i e^{2 pi i k/L} (dre + i dim) = -(s dre + c dim) + i (c dre - s dim)
+        v[b] = {F::norm(F::sub(pre, F::add(F::mul(s, dre), F::mul(c, dim)))),
+                F::norm(F::add(pim, F::sub(F::mul(c, dre), F::mul(s, dim))))};
+    }
+    fsync<T>();   // load() reads buf (the staged row): all reads precede the first pass's writes
+    // 2. FFT of length H
+    fft16<R, LOG2H>(v, buf, t, tw);
+    fsync<T>();
+}
+
+// c[f, n] = (-1)^n (2n+1) z_{i(n)} / M, n < N (or, with rowfn, the first
+// n_out coefficients of function rowfn[f] at c + out_off[.]).
+template <class R, int LOG2H>
+__global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dst16_forward_kernel(
+    const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
+    const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
+    const int *__restrict__ n_out)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
+    const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
+    const bool live = blockIdx.x * D::FPB + grp < B;
+    leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
+    using GT = typename Ar<R>::GT;
+    stage_row<R, LOG2H>(buf, G, ldg, f, t);
+    const GT *g = reinterpret_cast<const GT *>(buf);
+    dst16<R, LOG2H>(buf, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
+    if (!live) return;
+    typename Ar<R>::OUT *cf = c + (size_t)f * N;
+    int nn = N;
+    if (rowfn) {
+        const int fg = rowfn[f];
+        cf = c + out_off[fg];
+        nn = min(N, n_out[fg]);
+    }
+    constexpr int L = D::L;
+    constexpr int SHIFT = -(LOG2H + 2);   // 1 / M
+    for (int n = t; n < nn; n += D::T) {
+        const int i = (n & 1) ? L - 1 - (n >> 1) : (n >> 1);
+        const CxT<R> zz = buf[D::pc(i >> 1)];
+        T_ z = (i & 1) ? zz.im : zz.re;
+        if (n & 1) z = F::neg(z);
+        cf[n] = out_of(F::norm(F::mul(F::of_int(2 * n + 1), F::pow2(z, SHIFT))));
+    }
+}
+
+template <class R, int LOG2H>
+int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
+               const long long *out_off, const int *n_out)
+{
+    using D = D16<LOG2H>;
+    auto kern = dst16_forward_kernel<R, LOG2H>;
+    const size_t smem = d16_smem<R, LOG2H>();
+    LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (B + D::FPB - 1) / D::FPB;
+    // programmatic dependent launch, as the real-even transform
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(D::THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, static_cast<const typename Ar<R>::GT *>(G), ldg,
+                                    static_cast<typename Ar<R>::OUT *>(c), N, B,
+                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out));
+    return LEG_OK;
+}
+
+template <class R, int LO, int HI>
+int dispatch_fwd(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+                 const int *rowfn, const long long *out_off, const int *n_out)
+{
+    if constexpr (LO > HI) {
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
+    } else {
+        if (lg == LO) return launch_fwd<R, LO>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        return dispatch_fwd<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    }
+}
+
+}  // namespace
+
+// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768).  dtype
+// LEG_F64: FP64 G and c, table of double2; LEG_SPLIT_FP16: double-float G
+// (float2), FP32 c, table of float4; LEG_F32 / LEG_BF16: FP32 G and c,
+// table of float2.
+int leg_dst16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
+                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
+{
+    switch (dtype) {
+    case LEG_F64: return dispatch_fwd<double, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    case LEG_SPLIT_FP16: return dispatch_fwd<dfl, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    default: return dispatch_fwd<float, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    }
+}

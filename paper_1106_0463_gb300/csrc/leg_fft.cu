@@ -578,16 +578,21 @@ int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, c
 {
     if (B == 0) return LEG_OK;
     const int lg = ilog2(p->L);
+    if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H) {
+        const void *tw = p->dtype == LEG_F64 ? (const void *)p->tw64
+                         : p->dtype == LEG_SPLIT_FP16 ? (const void *)p->twdf : (const void *)p->tw32;
+        return leg_dst16_forward(p->dtype, lg - 1, G, ldg, c, p->N, B, tw, st, nullptr, nullptr, nullptr);
+    }
     switch (p->dtype) {
     case LEG_F64:
-        if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+        if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
         return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
         return dispatch_forward<float, 2, 14>(lg, G, ldg, c, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
-        if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+        if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c, p->N, B, p->twdf, st, nullptr, nullptr,
                                      nullptr);
         return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->twdf, st);
@@ -601,14 +606,14 @@ int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B
     const int lg = ilog2(p->L);
     switch (p->dtype) {
     case LEG_F64:
-        if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+        if (p->fft_variant != LEG_TRANSFORM_STOCKHAM && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_adjoint(LEG_F64, lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
         return dispatch_dct_adjoint<double, double, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
         return dispatch_adjoint<float, float, 2, 14>(lg, v, gbar, ldg, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
-        if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+        if (p->fft_variant != LEG_TRANSFORM_STOCKHAM && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_adjoint(LEG_SPLIT_FP16, lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
         return dispatch_dct_adjoint<dfl, float, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
     }
@@ -620,7 +625,9 @@ int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, 
 {
     if (B == 0) return LEG_OK;
     const int lg = ilog2(p->L);
-    if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+    if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
+        return leg_dst16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
+    if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
         return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
     return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
 }
@@ -633,7 +640,10 @@ int leg_fft_forward_ragged(const leg_plan *p, const void *G, int ldg, float *c_p
     if (B == 0) return LEG_OK;
     if (p->dtype != LEG_SPLIT_FP16) return leg_set_error(LEG_ERR_UNSUPPORTED, "ragged batches need split plans");
     const int lg = ilog2(p->L);
-    if (p->fft_variant == 0 && lg - 1 >= DCT16_MIN_LOG2H)
+    if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
+        return leg_dst16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off,
+                                 n_out);
+    if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
         return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off,
                                  n_out);
     return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off, n_out);

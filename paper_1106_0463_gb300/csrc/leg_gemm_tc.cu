@@ -928,10 +928,10 @@ int leg_build_split_transposed(leg_plan *p)
 {
     const int npr = leg_adj_depth(p);
     const size_t plane = (size_t)p->K * npr;
-    LEG_CUDA_TRY(cudaMalloc(&p->AhT[0], sizeof(__half) * 3 * plane));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->AhT[0], sizeof(__half) * 3 * plane));
     p->AhT[1] = p->AhT[0] + plane;
     p->AhT[2] = p->AhT[0] + 2 * plane;
-    LEG_CUDA_TRY(cudaMalloc(&p->colexp, sizeof(int) * p->K));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->colexp, sizeof(int) * p->K));
     split_cols_kernel<<<p->K, 256>>>(p->collapsed() ? p->L64 : p->A64, p->grows, p->K, npr, p->AhT[0], p->AhT[1],
                                      p->AhT[2], p->colexp, p->fbits);
     LEG_LAUNCH_CHECK("split_cols_kernel");

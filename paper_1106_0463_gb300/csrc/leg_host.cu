@@ -26,8 +26,8 @@ void leg_host_free(leg_plan *p)
 {
     LegHostState *h = p->host;
     if (!h) return;
-    cudaFree(h->f);
-    cudaFree(h->c);
+    leg_dev_free(h->f);
+    leg_dev_free(h->c);
     for (int i = 0; i < LEG_HOST_CHUNKS; ++i) {
         if (h->in[i]) cudaEventDestroy(h->in[i]);
         if (h->out[i]) cudaEventDestroy(h->out[i]);
@@ -60,12 +60,12 @@ int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
     LegHostState *h = p->host;
     if (B > h->cap) {
         LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
-        cudaFree(h->f);
-        cudaFree(h->c);
+        leg_dev_free(h->f);
+        leg_dev_free(h->c);
         h->f = h->c = nullptr;
         h->cap = 0;
-        LEG_CUDA_TRY(cudaMalloc(&h->f, eb * (size_t)B * p->K));
-        LEG_CUDA_TRY(cudaMalloc(&h->c, eb * (size_t)B * p->N));
+        LEG_CUDA_TRY(leg_dev_malloc(&h->f, eb * (size_t)B * p->K));
+        LEG_CUDA_TRY(leg_dev_malloc(&h->c, eb * (size_t)B * p->N));
         h->cap = B;
     }
     *out = h;

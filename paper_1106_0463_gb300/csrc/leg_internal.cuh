@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
 #include <string>
 
 #include "leg.h"
@@ -108,7 +109,7 @@ struct leg_plan {
     int *rowexp = nullptr;                        // per-row power-of-two scale (split)
     double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
     int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
-    int fft_variant = 0;      // 0: register-tiled transform (M >= 256), 1: shared-memory Stockham
+    int fft_variant = 0;      // LEG_TRANSFORM_*: the forward transform kernel (same map, rounding differs)
     bool collapsed() const { return (flags & LEG_FLAG_COLLAPSED) != 0; }
     // transposed split planes for the adjoint GEMM: K x Kpr (Kpr = rows padded),
     // each column k of the operator scaled by its own power of two
@@ -157,6 +158,34 @@ struct leg_plan {
 };
 
 void leg_host_free(leg_plan *p);
+// drops the one-call ragged batches built over plan p (leg_ragged.cu)
+void leg_ragged_forget_plan(const leg_plan *p);
+
+// ---------------------------------------------------------------------------
+// Device allocations of the library go through leg_dev_malloc (and
+// leg_dev_free).  With the
+// environment variable LEG_FAULT_ALLOC = k (k >= 1), the k-th call after the
+// variable took its current value fails with cudaErrorMemoryAllocation
+// without allocating anything: a host-side fault injection for the tests of
+// the LEG_ERR_OOM paths (no kernel ever sees a bad pointer).
+// ---------------------------------------------------------------------------
+cudaError_t leg_dev_malloc_bytes(void **ptr, size_t bytes);
+cudaError_t leg_dev_malloc_async_bytes(void **ptr, size_t bytes, cudaStream_t st);
+template <class T>
+inline cudaError_t leg_dev_malloc(T **ptr, size_t bytes)
+{
+    return leg_dev_malloc_bytes(reinterpret_cast<void **>(ptr), bytes);
+}
+// The matching releases (NULL accepted).  Together they keep the count and
+// bytes of the library's live device allocations (leg_memory_info).
+cudaError_t leg_dev_free(void *ptr);
+cudaError_t leg_dev_free_async(void *ptr, cudaStream_t st);
+
+// Tuning cache file (LEG_TUNE_CACHE): one "key a b" line per choice, the
+// last matching line wins (leg_tune.cu).  b may be NULL on lookup.
+std::mutex &leg_tune_mutex();
+bool leg_tune_cache_lookup(const char *path, const std::string &key, int *a, int *b);
+void leg_tune_cache_store(const char *path, const std::string &key, int a, int b);
 
 // Split input planes of a batch: LEG_SPLIT_NF FP16 planes of B rows with row
 // stride ld; plane s starts at base + s * pstride.
@@ -224,12 +253,28 @@ int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, c
 int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B, cudaStream_t st);
 int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, int B, cudaStream_t st);
 
+// Forward transform kernels of a plan (leg_plan::fft_variant).  All compute the
+// same linear map; their rounding differs.
+//   LEG_TRANSFORM_REG       register-tiled real-even transform (M >= 256; the
+//                           shared-memory one below that), FP32 plans: Stockham
+//   LEG_TRANSFORM_STOCKHAM  shared-memory Stockham transforms (leg_fft.cu)
+//   LEG_TRANSFORM_SINE      register-tiled half-range sine form, Eq. 2.13
+//                           (leg_dst16.cu; M >= 256)
+// The adjoint of every variant is the real-even adjoint (register-tiled unless
+// LEG_TRANSFORM_STOCKHAM is chosen).
+// (LEG_TRANSFORM_REG, LEG_TRANSFORM_STOCKHAM, LEG_TRANSFORM_SINE: leg.h)
+constexpr int LEG_TRANSFORM_MIN_M_REG = 256;   // smallest M of the register-tiled kernels (H = 64)
+
 // register-tiled transforms (leg_dct16.cu), H = 2^log2h with 6 <= log2h <= 13;
 // dtype LEG_F64 (FP64 G, c) or LEG_SPLIT_FP16 (double-float G, FP32 c)
 int leg_dct16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
                       cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
                       cudaStream_t st);
+// register-tiled sine form (leg_dst16.cu), same H range; dtype LEG_F64,
+// LEG_SPLIT_FP16 (double-float G, FP32 c) or LEG_F32 / LEG_BF16 (FP32)
+int leg_dst16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
+                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,

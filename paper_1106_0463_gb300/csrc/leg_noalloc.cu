@@ -14,8 +14,9 @@
 // reserved for the array until the process exits.  Host code cannot use the
 // array's name as a device address (on the host it names a host-side
 // stand-in), so on the first call on each device, with that device current,
-// the entry point looks the address up once with cudaGetSymbolAddress and
-// caches it; make that first call before any stream capture.  All calls on a
+// the entry point looks the address up with cudaGetSymbolAddress and caches
+// it with the device's context (a new context after cudaDeviceReset triggers
+// the lookup again); make that first call before any stream capture.  All calls on a
 // device share the one array, and it keeps the contents of the last call:
 // calls whose work overlaps on the GPU (for example on two streams) race on
 // it and must be serialised by the caller.  Nothing in the array needs to
@@ -36,22 +37,47 @@ static __device__ __align__(256) unsigned char g_leg_scratch[LEG_NOALLOC_SCRATCH
 
 std::mutex g_scratch_mutex;
 void *g_scratch_ptr[LEG_NOALLOC_MAX_DEVICES] = {};
+CUcontext g_scratch_ctx[LEG_NOALLOC_MAX_DEVICES] = {};   // the context the address belongs to
 
 size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
-// Device address of the scratch array on the current device (set-up on first use).
+// The current driver context (cuCtxGetCurrent through the runtime's entry
+// point lookup, so that the library needs no link against the driver library).
+int current_context(CUcontext *ctx)
+{
+    using GetCurrent = CUresult (*)(CUcontext *);
+    static GetCurrent fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !p)
+            return leg_set_error(LEG_ERR_CUDA, "leg_forward_noalloc: cuCtxGetCurrent entry point not found");
+        fn = reinterpret_cast<GetCurrent>(p);
+    }
+    if (fn(ctx) != CUDA_SUCCESS) return leg_set_error(LEG_ERR_CUDA, "leg_forward_noalloc: cuCtxGetCurrent failed");
+    return LEG_OK;
+}
+
+// Device address of the scratch array on the current device: looked up on the
+// first use, and again when the device's context has changed since (after a
+// cudaDeviceReset the array lives at a new address in the new context).
 int scratch_address(int dev, unsigned char **out)
 {
     if (dev < 0 || dev >= LEG_NOALLOC_MAX_DEVICES)
         return leg_set_error(LEG_ERR_UNSUPPORTED, "leg_forward_noalloc: device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    CUcontext ctx = nullptr;
+    int rc = current_context(&ctx);
+    if (rc) return rc;
+    if (!g_scratch_ptr[dev] || g_scratch_ctx[dev] != ctx) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_leg_scratch);
         if (e != cudaSuccess || !ptr)
             return leg_set_error(LEG_ERR_CUDA, std::string("leg_forward_noalloc: cudaGetSymbolAddress: ") +
                                                    cudaGetErrorString(e));
         g_scratch_ptr[dev] = ptr;
+        g_scratch_ctx[dev] = ctx;
     }
     *out = static_cast<unsigned char *>(g_scratch_ptr[dev]);
     return LEG_OK;

@@ -254,9 +254,9 @@ __global__ void twiddle_kernel(int M, double2 *t64, float2 *t32, float4 *tdf)
 
 int leg_build_twiddles(leg_plan *p)
 {
-    LEG_CUDA_TRY(cudaMalloc(&p->tw64, sizeof(double2) * p->M));
-    LEG_CUDA_TRY(cudaMalloc(&p->tw32, sizeof(float2) * p->M));
-    LEG_CUDA_TRY(cudaMalloc(&p->twdf, sizeof(float4) * p->M));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->tw64, sizeof(double2) * p->M));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->tw32, sizeof(float2) * p->M));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->twdf, sizeof(float4) * p->M));
     twiddle_kernel<<<(p->M + 255) / 256, 256>>>(p->M, p->tw64, p->tw32, p->twdf);
     LEG_LAUNCH_CHECK("twiddle_kernel");
     return LEG_OK;
@@ -271,7 +271,7 @@ int leg_build_operator(leg_plan *p)
 
     double *xh = nullptr, *wh = nullptr, *omxk = nullptr, *lam = nullptr;
     auto cleanup = [&]() {
-        cudaFree(xh); cudaFree(wh); cudaFree(omxk); cudaFree(lam);
+        leg_dev_free(xh); leg_dev_free(wh); leg_dev_free(omxk); leg_dev_free(lam);
     };
 #define LEG_TRY_CLEAN(expr)                                                         \
     do {                                                                            \
@@ -283,14 +283,14 @@ int leg_build_operator(leg_plan *p)
         }                                                                           \
     } while (0)
 
-    LEG_TRY_CLEAN(cudaMalloc(&xh, sizeof(double) * n_half));
-    LEG_TRY_CLEAN(cudaMalloc(&wh, sizeof(double) * n_half));
-    LEG_TRY_CLEAN(cudaMalloc(&p->omt2, sizeof(double) * Q));
-    LEG_TRY_CLEAN(cudaMalloc(&p->wq, sizeof(double) * Q));
+    LEG_TRY_CLEAN(leg_dev_malloc(&xh, sizeof(double) * n_half));
+    LEG_TRY_CLEAN(leg_dev_malloc(&wh, sizeof(double) * n_half));
+    LEG_TRY_CLEAN(leg_dev_malloc(&p->omt2, sizeof(double) * Q));
+    LEG_TRY_CLEAN(leg_dev_malloc(&p->wq, sizeof(double) * Q));
     double *omt2 = p->omt2, *wq = p->wq;
-    LEG_TRY_CLEAN(cudaMalloc(&omxk, sizeof(double) * K));
-    LEG_TRY_CLEAN(cudaMalloc(&lam, sizeof(double) * K));
-    LEG_TRY_CLEAN(cudaMalloc(&p->A64, sizeof(double) * (size_t)rows * K));
+    LEG_TRY_CLEAN(leg_dev_malloc(&omxk, sizeof(double) * K));
+    LEG_TRY_CLEAN(leg_dev_malloc(&lam, sizeof(double) * K));
+    LEG_TRY_CLEAN(leg_dev_malloc(&p->A64, sizeof(double) * (size_t)rows * K));
 
     gauss_legendre_half_kernel<<<(n_half + 127) / 128, 128>>>(n_rule, xh, wh);
     tau_rule_kernel<<<(Q + 127) / 128, 128>>>(Q, literal, xh, wh, omt2, wq);
@@ -316,29 +316,29 @@ int leg_build_collapsed(leg_plan *p)
     const int ldt = leg_round_up(rows, 8);
     double *AT = nullptr, *LT = nullptr;
     auto fail = [&](cudaError_t e, const char *what) {
-        cudaFree(AT);
-        cudaFree(LT);
+        leg_dev_free(AT);
+        leg_dev_free(LT);
         return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
                              std::string(what) + ": " + cudaGetErrorString(e));
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&AT, sizeof(double) * (size_t)K * ldt)) != cudaSuccess) return fail(e, "collapsed operator");
-    if ((e = cudaMalloc(&LT, sizeof(double) * (size_t)K * N)) != cudaSuccess) return fail(e, "collapsed operator");
-    if ((e = cudaMalloc(&p->L64, sizeof(double) * (size_t)N * K)) != cudaSuccess)
+    if ((e = leg_dev_malloc(&AT, sizeof(double) * (size_t)K * ldt)) != cudaSuccess) return fail(e, "collapsed operator");
+    if ((e = leg_dev_malloc(&LT, sizeof(double) * (size_t)K * N)) != cudaSuccess) return fail(e, "collapsed operator");
+    if ((e = leg_dev_malloc(&p->L64, sizeof(double) * (size_t)N * K)) != cudaSuccess)
         return fail(e, "collapsed operator");
     if ((e = cudaMemset(AT, 0, sizeof(double) * (size_t)K * ldt)) != cudaSuccess) return fail(e, "collapsed operator");
     transpose_f64(p->A64, K, AT, ldt, rows, K);
     int rc = leg_fft_forward_f64(p, AT, ldt, LT, K, 0);
     if (rc) {
-        cudaFree(AT);
-        cudaFree(LT);
+        leg_dev_free(AT);
+        leg_dev_free(LT);
         return rc;
     }
     transpose_f64(LT, N, p->L64, K, K, N);
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "collapsed operator");
     if ((e = cudaDeviceSynchronize()) != cudaSuccess) return fail(e, "collapsed operator");
-    cudaFree(AT);
-    cudaFree(LT);
+    leg_dev_free(AT);
+    leg_dev_free(LT);
     return LEG_OK;
 }
 
@@ -367,17 +367,17 @@ int leg_build_planes(leg_plan *p)
     } while (0)
     if (p->dtype == LEG_F32) {
         size_t n = (size_t)rows * K;
-        LEG_TRY_CLEAN(cudaMalloc(&p->A32, sizeof(float) * n));
+        LEG_TRY_CLEAN(leg_dev_malloc(&p->A32, sizeof(float) * n));
         plane_f32_kernel<<<(unsigned)((n + 255) / 256), 256>>>(S, p->A32, n);
     } else if (p->dtype == LEG_BF16) {
-        LEG_TRY_CLEAN(cudaMalloc(&p->Abf, sizeof(__nv_bfloat16) * (size_t)rows * p->Kp));
+        LEG_TRY_CLEAN(leg_dev_malloc(&p->Abf, sizeof(__nv_bfloat16) * (size_t)rows * p->Kp));
         plane_bf16_kernel<<<rows, 256>>>(S, K, p->Kp, p->Abf);
     } else if (p->dtype == LEG_SPLIT_FP16) {
         const size_t plane = (size_t)rows * p->Kp;
-        LEG_TRY_CLEAN(cudaMalloc(&p->Ah[0], sizeof(__half) * 3 * plane));
+        LEG_TRY_CLEAN(leg_dev_malloc(&p->Ah[0], sizeof(__half) * 3 * plane));
         p->Ah[1] = p->Ah[0] + plane;
         p->Ah[2] = p->Ah[0] + 2 * plane;
-        LEG_TRY_CLEAN(cudaMalloc(&p->rowexp, sizeof(int) * rows));
+        LEG_TRY_CLEAN(leg_dev_malloc(&p->rowexp, sizeof(int) * rows));
         plane_split_kernel<<<rows, 256>>>(S, K, p->Kp, p->Ah[0], p->Ah[1], p->Ah[2], p->rowexp, p->fbits);
         LEG_TRY_CLEAN(cudaGetLastError());
         int rc2 = leg_build_split_transposed(p);

@@ -4,7 +4,9 @@
 //     g_j = sum_q w_q f(x_jq),   1 - x_jq = 2 sin^2(pi j / M) (1 - tau_q^2),
 // for the rows j = 0..M/2 of the grid y_j = 2 pi j / M, in FP64.  The result
 // feeds the same FFT stage as the sampled path.  Families: the generating
-// function (Eq. 2.2), e^{ax}, and Chebyshev series given by coefficients.
+// function (Eq. 2.2), e^{ax}, |x|^alpha (the test function of Table 1, whose
+// coefficients Eq. 2.15 gives in closed form), and Chebyshev series given by
+// coefficients.
 #include "leg_internal.cuh"
 
 namespace {
@@ -15,6 +17,11 @@ __device__ __forceinline__ double closed_form(int family, double par, double omx
         // (1 - 2 x t + t^2)^(-1/2) with x = 1 - omx:  (1 - t)^2 + 2 t omx
         double om = 1.0 - par;
         return rsqrt(om * om + 2.0 * par * omx);
+    }
+    if (family == LEG_FAMILY_ABSPOW) {
+        // |x|^alpha (Table 1: alpha = 3/2); |x| = |1 - omx|, 0^alpha = 0
+        const double ax = fabs(1.0 - omx);
+        return ax > 0.0 ? pow(ax, par) : 0.0;
     }
     // exp(a x)
     return exp(par * (1.0 - omx));

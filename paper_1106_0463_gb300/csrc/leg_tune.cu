@@ -4,14 +4,17 @@
 //   * tile width of the split-FP16 / BF16 tensor-core GEMM (functions per CTA
 //     pair tile): the cost model's choice and the multiples of 16 from the
 //     plan's maximum down to 64;
-//   * transform kernel of the FP64 / double-float FFT stage: the
-//     register-tiled real-even transform or the shared-memory Stockham one.
+//   * transform kernel of the FFT stage: the register-tiled real-even
+//     transform, the shared-memory Stockham one, or the register-tiled sine
+//     form (Eq. 2.13); plans created with LEG_FLAG_SINE_FORM keep the sine
+//     form.
 //
 // Each candidate runs once untimed and three times timed (CUDA events around
 // the stage, on the caller's stream); the fastest median wins and is stored
 // in the plan.  With the environment variable LEG_TUNE_CACHE naming a file,
-// choices are kept there, one line per (device, dtype, N, M, K, B), and a
-// later call with the same key takes the stored choice without timing.
+// choices are kept there, one line per (device, dtype, N, M, K, Q, flags, B),
+// and a later call with the same key takes the stored choice without timing
+// (a stored choice outside the plan's valid range is ignored and re-timed).
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -23,9 +26,40 @@
 
 #include "leg_internal.cuh"
 
-namespace {
+std::mutex &leg_tune_mutex()
+{
+    static std::mutex m;
+    return m;
+}
 
-std::mutex g_tune_mutex;
+bool leg_tune_cache_lookup(const char *path, const std::string &key, int *a_out, int *b_out)
+{
+    FILE *fp = fopen(path, "r");
+    if (!fp) return false;
+    char line[2048];
+    bool found = false;
+    while (fgets(line, sizeof(line), fp)) {
+        char k[1900];
+        int a = 0, b = 0;
+        if (sscanf(line, "%1899s %d %d", k, &a, &b) == 3 && key == k) {
+            *a_out = a;
+            if (b_out) *b_out = b;
+            found = true;   // the last matching line wins
+        }
+    }
+    fclose(fp);
+    return found;
+}
+
+void leg_tune_cache_store(const char *path, const std::string &key, int a, int b)
+{
+    FILE *fp = fopen(path, "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d %d\n", key.c_str(), a, b);
+    fclose(fp);
+}
+
+namespace {
 
 std::string tune_key(const leg_plan *p, int B)
 {
@@ -35,35 +69,9 @@ std::string tune_key(const leg_plan *p, int B)
     for (auto &ch : dev)
         if (ch == ' ' || ch == '|') ch = '_';
     char buf[256];
-    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|%d", dev.c_str(), p->dtype, p->N, p->M, p->K, p->Q, B);
+    snprintf(buf, sizeof(buf), "%s|%d|%d|%d|%d|%d|%u|%d", dev.c_str(), p->dtype, p->N, p->M, p->K, p->Q, p->flags,
+             B);
     return buf;
-}
-
-bool cache_lookup(const char *path, const std::string &key, int *tn, int *fft)
-{
-    FILE *fp = fopen(path, "r");
-    if (!fp) return false;
-    char line[512];
-    bool found = false;
-    while (fgets(line, sizeof(line), fp)) {
-        char k[400];
-        int a = 0, b = 0;
-        if (sscanf(line, "%399s %d %d", k, &a, &b) == 3 && key == k) {
-            *tn = a;
-            *fft = b;
-            found = true;   // the last matching line wins
-        }
-    }
-    fclose(fp);
-    return found;
-}
-
-void cache_store(const char *path, const std::string &key, int tn, int fft)
-{
-    FILE *fp = fopen(path, "a");
-    if (!fp) return;
-    fprintf(fp, "%s %d %d\n", key.c_str(), tn, fft);
-    fclose(fp);
 }
 
 // Median of `reps` timings of stage `stage` (0 split, 1 GEMM, 2 FFT) of the forward pass.
@@ -90,18 +98,26 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
     if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
     if (B < 1) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 1");
     if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
-    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    std::lock_guard<std::mutex> lock(leg_tune_mutex());
     const char *path = getenv("LEG_TUNE_CACHE");
     const std::string key = tune_key(p, B);
     int tn = p->tn, fft = p->fft_variant;
-    if (path && *path && cache_lookup(path, key, &tn, &fft)) {
+    const bool tc = (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16);
+    const int maxtn = (p->dtype == LEG_BF16) ? 256 : 128;
+    const bool sine_fixed = (p->flags & LEG_FLAG_SINE_FORM) != 0;
+    auto valid = [&](int w, int v) {
+        const bool tn_ok = w == 0 || (tc && w >= 16 && w <= maxtn && w % 16 == 0);
+        const bool fft_ok = v >= LEG_TRANSFORM_REG && v <= LEG_TRANSFORM_SINE &&
+                            (v != LEG_TRANSFORM_SINE || p->M >= LEG_TRANSFORM_MIN_M_REG) &&
+                            (!sine_fixed || v == LEG_TRANSFORM_SINE);
+        return tn_ok && fft_ok;
+    };
+    if (path && *path && leg_tune_cache_lookup(path, key, &tn, &fft) && valid(tn, fft)) {
         p->tn = tn;
         p->fft_variant = fft;
     } else {
         int rc;
-        const bool tc = (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16);
         if (tc) {
-            const int maxtn = (p->dtype == LEG_BF16) ? 256 : 128;
             std::vector<int> cand = {0};
             for (int w = maxtn; w >= 64; w -= 16) cand.push_back(w);
             float best = -1.0f;
@@ -120,18 +136,29 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
             }
             p->tn = best_tn;
         }
-        if ((p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) && !p->collapsed()) {   // collapsed: no transform
-            float t0 = 0.0f, t1 = 0.0f;
-            p->fft_variant = 0;
-            if ((rc = time_stage(p, f, c, B, st, 2, 3, &t0))) return rc;
-            p->fft_variant = 1;
-            if ((rc = time_stage(p, f, c, B, st, 2, 3, &t1))) {
-                p->fft_variant = 0;
-                return rc;
+        if (!p->collapsed() && !sine_fixed) {   // collapsed: no transform; sine form: the caller's choice
+            // FP32 plans have one real-even kernel (Stockham) besides the sine form
+            std::vector<int> cand;
+            if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) cand = {LEG_TRANSFORM_REG, LEG_TRANSFORM_STOCKHAM};
+            else cand = {LEG_TRANSFORM_REG};
+            if (p->M >= LEG_TRANSFORM_MIN_M_REG) cand.push_back(LEG_TRANSFORM_SINE);
+            float best = -1.0f;
+            int best_v = LEG_TRANSFORM_REG;
+            for (int v : cand) {
+                p->fft_variant = v;
+                float t;
+                if ((rc = time_stage(p, f, c, B, st, 2, 3, &t))) {
+                    p->fft_variant = LEG_TRANSFORM_REG;
+                    return rc;
+                }
+                if (best < 0 || t < best * 0.99f) {   // ties stay with the earlier candidate
+                    best = t;
+                    best_v = v;
+                }
             }
-            p->fft_variant = (t1 < t0 * 0.99f) ? 1 : 0;
+            p->fft_variant = best_v;
         }
-        if (path && *path) cache_store(path, key, p->tn, p->fft_variant);
+        if (path && *path) leg_tune_cache_store(path, key, p->tn, p->fft_variant);
     }
     if (tn_out) *tn_out = p->tn;
     if (fft_out) *fft_out = p->fft_variant;
