@@ -109,9 +109,9 @@ def test_forward_host_fails_cleanly(leg, monkeypatch):
 
 
 def test_plain_method_scratch_fails_cleanly(leg, monkeypatch):
-    # a split plan's G holds double-float pairs: the FP64 plain method takes a
-    # stream-ordered allocation for its G
-    plan = leg.Plan(64, 256, 17, 32, leg.SPLIT_FP16)
+    # an FP32 plan's G holds 4-byte values: the FP64 plain method takes a
+    # stream-ordered allocation for its G (after the plan's workspace)
+    plan = leg.Plan(64, 256, 17, 32, leg.F32)
     params = torch.tensor([0.5, 0.3], dtype=torch.float64, device="cuda")
     ref = leg.Plan(64, 256, 17, 32, leg.F64).plain_forward(leg.FAMILY_GENFN, params)
     n, c = sweep(leg, monkeypatch, lambda: plan.plain_forward(leg.FAMILY_GENFN, params))
