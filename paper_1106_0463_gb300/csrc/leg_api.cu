@@ -62,10 +62,20 @@ size_t g_elem_bytes(int dtype)
     }
 }
 
+int alloc_workspace(leg_plan *p, int B);
+
+// Grow the workspace to B functions; on failure nothing of it stays allocated.
 int ensure_workspace(leg_plan *p, int B)
 {
     if (B <= p->ws_B) return LEG_OK;
     free_workspace(p);
+    const int rc = alloc_workspace(p, B);
+    if (rc) free_workspace(p);
+    return rc;
+}
+
+int alloc_workspace(leg_plan *p, int B)
+{
     const size_t eb = g_elem_bytes(p->dtype);
     const size_t Bz = (size_t)B;
     const int rowsKp = leg_round_up(p->rows, 8);

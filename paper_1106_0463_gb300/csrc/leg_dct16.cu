@@ -115,8 +115,8 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dct
     using T_ = typename F::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
-    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
-    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * D::SLOTS) + grp * D::WARPS;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
+    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * gslots<R, LOG2H>()) + grp * D::WARPS;
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
     constexpr int L = D::L;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
-    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
-    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * D::SLOTS) + grp * D::WARPS;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
+    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * gslots<R, LOG2H>()) + grp * D::WARPS;
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);
     const bool live = blockIdx.x * D::FPB + grp < B;
     const VIN *vf = v + (size_t)f * N;

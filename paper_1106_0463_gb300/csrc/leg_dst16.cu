@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dst
     using T_ = typename F::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
-    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * D::SLOTS;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G

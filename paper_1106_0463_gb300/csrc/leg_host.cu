@@ -64,8 +64,15 @@ int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
         leg_dev_free(h->c);
         h->f = h->c = nullptr;
         h->cap = 0;
-        LEG_CUDA_TRY(leg_dev_malloc(&h->f, eb * (size_t)B * p->K));
-        LEG_CUDA_TRY(leg_dev_malloc(&h->c, eb * (size_t)B * p->N));
+        cudaError_t e = leg_dev_malloc(&h->f, eb * (size_t)B * p->K);
+        if (e == cudaSuccess) e = leg_dev_malloc(&h->c, eb * (size_t)B * p->N);
+        if (e != cudaSuccess) {   // release what was taken: nothing stays half-grown
+            leg_dev_free(h->f);
+            leg_dev_free(h->c);
+            h->f = h->c = nullptr;
+            return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
+                                 std::string("leg_forward_host device copies: ") + cudaGetErrorString(e));
+        }
         h->cap = B;
     }
     *out = h;

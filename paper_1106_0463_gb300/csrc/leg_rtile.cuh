@@ -232,6 +232,17 @@ template <int LOG2H> struct D16 {
     static __device__ __forceinline__ int px(int i) { return i + (i >> (LOG2E + 1)); }
 };
 
+// Complex slots between consecutive functions' exchange buffers for the
+// arithmetic type R: D16::SLOTS, rounded up so that every buffer starts on a
+// 16-byte boundary (the row staging copies 16 bytes at a time).  SLOTS is odd,
+// so 8-byte complex values (FP32) take one more slot; 16-byte ones keep SLOTS.
+template <class R, int LOG2H>
+__host__ __device__ constexpr int gslots()
+{
+    constexpr int S = D16<LOG2H>::SLOTS;
+    return (S * (int)sizeof(CxT<R>)) % 16 == 0 ? S : S + (16 / (int)sizeof(CxT<R>)) - 1;
+}
+
 template <int T>
 __device__ __forceinline__ void fsync()
 {
@@ -409,6 +420,7 @@ __device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT 
     using GT = typename Ar<R>::GT;
     constexpr int BYTES = ((D::L + 1) * (int)sizeof(GT) + 15) / 16 * 16;
     static_assert(BYTES <= D::SLOTS * (int)sizeof(CxT<R>), "row of G exceeds the exchange buffer");
+    static_assert((gslots<R, LOG2H>() * (int)sizeof(CxT<R>)) % 16 == 0, "exchange buffers must be 16-byte aligned");
     const char *src = reinterpret_cast<const char *>(G + (size_t)f * ldg);
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
     for (int o = 16 * t; o < BYTES; o += 16 * D::T)
@@ -453,7 +465,7 @@ template <class R, int LOG2H>
 size_t d16_smem()
 {
     using D = D16<LOG2H>;
-    return sizeof(CxT<R>) * D::FPB * D::SLOTS + sizeof(typename Fa<R>::T) * D::FPB * D::WARPS;
+    return sizeof(CxT<R>) * D::FPB * gslots<R, LOG2H>() + sizeof(typename Fa<R>::T) * D::FPB * D::WARPS;
 }
 
 }  // namespace

@@ -1,13 +1,18 @@
 """Full-size workloads on the GPU, checked on sampled outputs the oracle can compute.
 
-* B=4096, K=1025, N=512, M=2048 (the bench workload): split-FP16 and the plain
-  FP32 / FP64 paths, 16 sampled functions against oracle route 2.
+* B=4096, K=1025, N=512, M=2048: split-FP16 and the plain FP32 / FP64 paths,
+  the first and last function of every GEMM function tile plus 16 more
+  against oracle route 1 (an exact configuration).
 * Precision sweep B=256, K=8193, N=4096, M=16384 (rho up to 0.999): FP64, FP32,
-  BF16 and split-FP16 from one operator, 4 sampled functions against oracle
-  route 1 (the configuration is exact for polynomial inputs: M > N + K - 1 with
-  the exact tau rule, so routes 1 and 2 agree to rounding).
-* Differentiation B=1024, K=4097, N=2048, M=8192: torch.autograd gradients of
-  sum_n w_n (c_n - c*_n)^2 (FP64 path and split path) against FP64 central
+  BF16 and split-FP16 from one operator, 40 sampled functions (the first and
+  last of every GEMM function tile among them) against oracle route 1 (the
+  configuration is exact for polynomial inputs: M > N + K - 1 with the exact
+  tau rule, so routes 1 and 2 agree to rounding).
+* Differentiation B=1024, K=4097, N=2048, M=8192: forward parity on >= 16
+  sampled functions (first and last of every function tile); the adjoint
+  df = L^T v element by element against the oracle's route 1 transposed on the
+  same functions (split 1e-6, FP64 1e-11 of max|df|); torch.autograd gradients
+  of sum_n w_n (c_n - c*_n)^2 (FP64 path and split path) against FP64 central
   differences on 64 random directions, and the split adjoint against the
   oracle's forward through <L f, v> = <f, L^T v>.
 Errors are max_n |c - c_ref| / max_n |c_ref| per function, max over the sample.
@@ -40,14 +45,25 @@ def forward(leg, plan, f_np):
     return c.double().cpu().numpy()
 
 
+def tile_sample(B, tn, extra, seed):
+    """The first and last function of every GEMM function tile of width tn,
+    plus `extra` more at random."""
+    idx = set()
+    for t0 in range(0, B, tn):
+        idx.update((t0, min(B, t0 + tn) - 1))
+    rest = np.setdiff1d(np.arange(B), sorted(idx))
+    idx.update(int(i) for i in np.random.default_rng(seed).choice(rest, size=min(extra, rest.size), replace=False))
+    return np.array(sorted(idx))
+
+
 def test_bench_workload_all_paths(leg, oracle):
     name = "cheb_b4096_k1025_n512_m2048"
     cfg = workloads.CONFIGS[name]
     f = workloads.workload_inputs(name)
-    sample = np.array([0, 1, 2, 777, 2048, 3000, 4094, 4095, 5, 6, 7, 100, 1000, 1500, 2500, 3500])
-    ref = oracle.coeffs_abel(cfg["N"], cfg["M"], oracle.exact_tau_points(cfg["K"]),
-                             f_cl=f[sample].astype(np.float64))
     split = leg.Plan(cfg["N"], cfg["M"], cfg["K"], 0, leg.SPLIT_FP16)
+    sample = tile_sample(cfg["B"], split.tile_info(cfg["B"])["tn"], 16, 2)
+    # exact configuration (M > N + K - 1, exact tau rule): route 1
+    ref = oracle.coeffs_direct(cfg["N"], (cfg["K"] + cfg["N"]) // 2 + 4, f_cl=f[sample].astype(np.float64))
     errs = {"split": relerr(forward(leg, split, f)[sample], ref)}
     for name_, dt in (("f32", leg.F32), ("f64", leg.F64)):
         errs[name_] = relerr(forward(leg, leg.Plan.like(split, dt), f)[sample], ref)
@@ -62,9 +78,11 @@ def test_precision_sweep(leg, oracle):
     cfg = workloads.CONFIGS[name]
     N, M, K = cfg["N"], cfg["M"], cfg["K"]
     f = workloads.workload_inputs(name)
-    sample = np.array([0, 101, 200, 255])
-    ref = oracle.coeffs_direct(N, (K + N) // 2 + 4, f_cl=f[sample].astype(np.float64))
     base = leg.Plan(N, M, K, 0, leg.F64)
+    tn = leg.Plan.like(base, leg.SPLIT_FP16).tile_info(cfg["B"])["tn"]
+    sample = tile_sample(cfg["B"], tn, 36, 3)
+    assert len(sample) >= 32
+    ref = oracle.coeffs_direct(N, (K + N) // 2 + 4, f_cl=f[sample].astype(np.float64))
     errs = {"f64": relerr(forward(leg, base, f)[sample], ref)}
     for name_, dt in (("f32", leg.F32), ("bf16", leg.BF16), ("split_fp16", leg.SPLIT_FP16)):
         errs[name_] = relerr(forward(leg, leg.Plan.like(base, dt), f)[sample], ref)
@@ -87,11 +105,23 @@ def test_differentiation(leg, oracle):
     tgt = torch.tensor(tgt_np, device="cuda")
 
     # forward parity on sampled functions (route 1: exact configuration)
-    sample = np.array([0, 511, 1023])
-    ref = oracle.coeffs_direct(N, (K + N) // 2 + 4, f_cl=f_np[sample].astype(np.float64))
+    sample = tile_sample(B, split.tile_info(B)["tn"], 8, 4)
+    assert len(sample) >= 16
+    Qo = (K + N) // 2 + 4
+    ref = oracle.coeffs_direct(N, Qo, f_cl=f_np[sample].astype(np.float64))
     x32 = torch.from_numpy(f_np).cuda().requires_grad_(True)
     c32 = leg.legendre(x32, split)
     assert relerr(c32.detach().double().cpu().numpy()[sample], ref) < 1e-6
+
+    # the adjoint element by element against the oracle's route 1 transposed
+    # (df = L^T v for random v), split and FP64
+    vv = np.random.default_rng(8).standard_normal((B, N))
+    ref_b = oracle.adjoint_direct(Qo, K, vv[sample])
+    for pl, tdt, tol in ((split, torch.float32, 1e-6), (f64, torch.float64, 1e-11)):
+        dfv = pl.backward(torch.from_numpy(vv).to(device="cuda", dtype=tdt)).double().cpu().numpy()[sample]
+        eb = relerr(dfv, ref_b)
+        print("adjoint vs oracle route 1 transposed", pl.dtype, eb)
+        assert eb < tol
 
     # end-to-end gradient of the split-path loss through LegendreFn
     (w.float() * (c32 - tgt.float()) ** 2).sum().backward()

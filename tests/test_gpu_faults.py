@@ -35,6 +35,8 @@ def sweep(leg, monkeypatch, attempt, max_k=100):
     """attempt() under LEG_FAULT_ALLOC = 1, 2, ... until it succeeds; returns
     (number of allocations the call makes, the successful result).  After
     every failed attempt the library holds exactly what it held before."""
+    import gc
+    gc.collect()   # plans other tests left to the collector release their memory now
     base = free_bytes()
     held = leg.memory_info()
     for k in range(1, max_k):
@@ -43,7 +45,6 @@ def sweep(leg, monkeypatch, attempt, max_k=100):
             obj = attempt()
         except leg.LegError as e:
             assert e.code == 2, (k, str(e))   # LEG_ERR_OOM
-            import gc
             gc.collect()
             assert leg.memory_info() == held, (k, held, leg.memory_info())
             assert abs(free_bytes() - base) <= SLACK, (k, base - free_bytes())
@@ -58,6 +59,8 @@ def sweep(leg, monkeypatch, attempt, max_k=100):
 def test_plan_create_fails_cleanly(leg, monkeypatch, dtype_name, flags):
     dt = getattr(leg, dtype_name)
     leg.Plan(64, 256, 65, 0, dt, flags=flags).close()   # loads the kernels once
+    import gc
+    gc.collect()
     base = free_bytes()
     held = leg.memory_info()
     n, plan = sweep(leg, monkeypatch, lambda: leg.Plan(64, 256, 65, 0, dt, flags=flags))
@@ -66,6 +69,7 @@ def test_plan_create_fails_cleanly(leg, monkeypatch, dtype_name, flags):
     assert leg.memory_info() == held
     assert abs(free_bytes() - base) <= SLACK
     like = leg.Plan(64, 256, 65, 0, leg.F64)
+    gc.collect()
     base = free_bytes()
     held = leg.memory_info()
     n, p2 = sweep(leg, monkeypatch, lambda: leg.Plan.like(like, dt))
