@@ -64,6 +64,11 @@ def parse():
     ap.add_argument("--path", default="split_fp16", choices=["split_fp16", "f32", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
+    ap.add_argument("--tile", type=int, default=None,
+                    help="GEMM tile width of the headline plan (0 = the library's model); with --transform, "
+                         "skips the autotuner")
+    ap.add_argument("--transform", default=None, choices=["reg", "stockham", "sine"],
+                    help="transform kernel of the headline plan")
     return ap.parse_args()
 
 
@@ -241,6 +246,8 @@ DTYPE_STR = {
     "f32": "f32", "bf16": "bf16 (f32 accum) + f32 FFT", "f64": "f64",
 }
 PRODUCTS = {"split_fp16": 8, "bf16": 1, "f32": 1, "f64": 1}
+TRANSFORM_NAMES = {0: "register-tiled real-even (Eq. 2.4 with the twist as a first difference)",
+                   1: "shared-memory Stockham real-even", 2: "register-tiled sine form (Eq. 2.13)"}
 LAUNCHES = {"split_fp16": 3, "bf16": 3, "f32": 2, "f64": 2}
 
 # Peak arithmetic rates of the FFT stage (ops/s in units of 1e12), from unit
@@ -254,22 +261,23 @@ ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 TRAFFIC = {}
 
 
-def fft_fp32_ops(M, N):
+def fft_fp32_ops(M, N, fp64=False):
     """FP32 operations of the double-float real-even transform of one function
     (the algorithmic operation count of the FFT stage at the precision it
     needs): a length-H complex FFT (H = M/4) with (H/2) log2 H radix-2
     butterflies of 4 mul + 6 add, the fold (L = M/2 values: 3.5 add + 2.5 mul
     each), the recombination (H x 8 add + 4 mul), the scan (H add) and the
     output (N x 1 add + 1 mul), each double-float add costing 8 FP32 operations
-    (TwoSum + trailing add) and each multiply 4 (exact product by FMA + 2 FMA)."""
+    (TwoSum + trailing add) and each multiply 4 (exact product by FMA + 2 FMA);
+    with fp64, one FP64 operation each."""
     H, L = M // 4, M // 2
     lg = int(round(np.log2(H)))
     adds = 3 * H * lg + 3.5 * L + 8 * H + H + N
     muls = 2 * H * lg + 2.5 * L + 4 * H + N
-    return 8 * adds + 4 * muls
+    return adds + muls if fp64 else 8 * adds + 4 * muls
 
 
-def dst_fp32_ops(M, N):
+def dst_fp32_ops(M, N, fp64=False):
     """FP32 operations of the double-float sine-form transform (Eq. 2.13) of
     one function, same conventions: the length-H FFT, the merged pre-twiddle
     (two W values per k < H: 3 add + 2 mul each; their sum and difference:
@@ -279,7 +287,7 @@ def dst_fp32_ops(M, N):
     lg = int(round(np.log2(H)))
     adds = 3 * H * lg + 14 * H
     muls = 2 * H * lg + 8 * H + 2 * N
-    return 8 * adds + 4 * muls
+    return adds + muls if fp64 else 8 * adds + 4 * muls
 
 
 def relerr(c, ref):
@@ -333,7 +341,8 @@ def fft_roofline(B, M, N, rows, path, fft_ms, peaks, peak_src, traffic, name, si
     hbm_gbs = bytes_ / sec / 1e9
     kern = "dst16_forward_kernel (sine form)" if sine else "dct16_forward_kernel (real-even)"
     if path in ("split_fp16", "f64"):
-        ops = (dst_fp32_ops(M, N) if sine else fft_fp32_ops(M, N)) * B
+        # double-float: FP32 operations; FP64: one operation per FP64 add or multiply
+        ops = (dst_fp32_ops(M, N, path == "f64") if sine else fft_fp32_ops(M, N, path == "f64")) * B
         peak = ALU_PEAK_TOPS["f64" if path == "f64" else "f32"]
         r = {"kernel": kern, "bound": "alu", "achieved": ops / sec / 1e12, "peak": peak, "unit": "Tops/s",
              "ops_per_launch": ops, "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz max SM clock"
@@ -415,6 +424,25 @@ class Dense:
             self.torch.cuda.synchronize()
             self.plan_s[path] = time.time() - t0
         return self.plans[path]
+
+    def autotune(self, path):
+        """leg_plan_autotune on this batch: GEMM tile width and transform kernel."""
+        plan = self.plan(path)
+        c = self.torch.empty((self.B, self.N), dtype=plan.io_dtype, device="cuda")
+        choice = plan.autotune(self.inputs(path), c)
+        if path == "split_fp16":
+            self.retile()
+        return choice
+
+    def retile(self):
+        """Sampled rows for the split plan's current tile width."""
+        tn = self.plans["split_fp16"].tile_info(self.B)["tn"]
+        if tn != self.tn:
+            self.tn = tn
+            self.sample = sample_rows(self.B, self.tn, 36, 7)
+            if self.ref is not None:
+                from oracle import oracle as O
+                self.ref = oracle_coeffs(O, self.name, self.f_np[self.sample].astype(np.float64))
 
     def inputs(self, path):
         torch = self.torch
@@ -510,7 +538,7 @@ def table1_plain(leg, torch, O):
     return out
 
 
-def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref):
+def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3):
     """The ragged workload: 10,000 closed-form functions in 9 size buckets,
     one grouped persistent GEMM launch, replayed as a CUDA graph."""
     cfg = workloads.CONFIGS["ragged_10000"]
@@ -528,9 +556,11 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref):
                   dev(lay["in_off"], torch.int64), f, coef=dev(lay["coef"], torch.float64),
                   coef_off=dev(lay["coef_off"], torch.int64))
     c = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
-    ts, _ = time_steps(torch, lambda: batch.forward(f, c), flush, 20, 3)
+    model_tn = batch.tile_info()["tn"]
+    tuned_tn = batch.autotune(f, c)   # the grouped launch's tile width, timed on this batch
+    ts, _ = time_steps(torch, lambda: batch.forward(f, c), flush, steps, warmup)
     st = []
-    for _ in range(5):
+    for _ in range(min(5, steps)):
         flush.zero_()
         st.append(batch.forward_profiled(f, c))
     batch.forward(f, c)
@@ -557,7 +587,8 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref):
     out = {"value": float(np.sum(n)) / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "functions": cfg["count"],
            "coefficients": int(np.sum(n)), "buckets": lay["buckets"], "plan_build_s": setup,
            "stages_ms": {"input_split": split_ms, "grouped_gemm": gemm_ms, "transforms": fft_ms},
-           "roofline": roof, "tile_width": batch.tile_info()["tn"],
+           "roofline": roof, "tile_width": tuned_tn, "tile_width_cost_model": model_tn,
+           "tile_chosen_by": "leg_ragged_autotune (timed candidates: the cost model's width and 128..64)",
            "gpu_launches_per_step": 2 + len(lay["buckets"]), "cuda_graph": True}
     if with_ref:
         from oracle import oracle as O
@@ -659,6 +690,25 @@ def whole_job_rate(world: int, units_per_rank: int, ms_per_step: float) -> float
     return world * units_per_rank / (ms_per_step / 1e3)
 
 
+def ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
+    """--workload ragged_10000: the ragged batch as the timed workload."""
+    r = ragged(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup)
+    ms = max_over_ranks(torch, dist, r["ms_per_step"], "cuda")
+    if rank == 0:
+        line = {"metric": METRIC, "value": whole_job_rate(world, r["coefficients"], ms), "unit": UNIT,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_STR["split_fp16"],
+                "data": "synthetic",
+                "config": {"workload": "ragged_10000", "functions": r["functions"], "buckets": r["buckets"],
+                           "l2": "flushed (512 MiB write) before every timed step"},
+                "max_rel_err": r.get("max_rel_err"), "err_sample": r.get("err_sample"), "roofline": r["roofline"],
+                "stages_ms": r["stages_ms"], "gpu_launches": r["gpu_launches_per_step"] * args.steps}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import paper_1106_0463_gb300 as leg
@@ -672,15 +722,30 @@ def gpu_arm(args, rank, world, local_rank):
     peaks, peak_src = load_peaks()
     flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     with_ref = rank == 0
+    if name == "ragged_10000":
+        ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src)
+        return
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
-    # ---------------- the headline: timed region on the selected path
+    # ---------------- the headline: tuned, then the timed region on the selected path
     head = Dense(leg, torch, name, rank, with_ref, extra=36)
     B, N = head.B, head.N
+    if args.tile is not None and args.transform is not None:
+        plan = head.plan(args.path)
+        if args.path in ("split_fp16", "bf16"):
+            plan.set_tile(args.tile)
+        plan.set_transform({"reg": leg.TRANSFORM_REG, "stockham": leg.TRANSFORM_STOCKHAM,
+                            "sine": leg.TRANSFORM_SINE}[args.transform])
+        tuned = {"tn": args.tile, "fft": plan.transform, "source": "command line"}
+        if args.path == "split_fp16":
+            head.retile()
+    else:
+        tuned = head.autotune(args.path)   # GEMM tile width and transform kernel, timed on this batch
+        tuned["source"] = "leg_plan_autotune on this batch"
     barrier()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local_rank].strip() if vis else str(local_rank)
@@ -725,6 +790,8 @@ def gpu_arm(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": DTYPE_STR[args.path], "data": "synthetic",
         "config": {"workload": name, "B": B, "K": head.K, "N": N, "M": head.M, "Q": (head.K + 1) // 2,
                    "path": args.path, "tile_width": head.tn,
+                   "launch_settings": {"tile_width_setting": tuned["tn"],
+                                       "transform": TRANSFORM_NAMES[tuned["fft"]], "chosen_by": tuned["source"]},
                    "l2": "flushed (512 MiB write) before every timed step; the operator planes (%.0f MB) also "
                          "exceed L2" % (3 * (head.rows - 1) * head.Kp * 2 / 1e6),
                    "inputs": "random decaying Chebyshev series sampled at CL nodes, FP32, seeded"},
@@ -746,9 +813,9 @@ def gpu_arm(args, rank, world, local_rank):
                         "stages_ms": r["stages_ms"]}
         wl["precision_sweep_" + name] = sweep
         line["speedup_vs_fp64_gpu_path"] = (value / world) / sweep["f64"]["value"]
-        if args.path in ("split_fp16", "f64", "f32", "bf16"):
-            r = head.run(args.path, flush, 20, 3, peaks, peak_src, transform=leg.TRANSFORM_SINE)
-            wl["sine_form_" + name] = strip(r)
+        other = leg.TRANSFORM_REG if tuned["fft"] == leg.TRANSFORM_SINE else leg.TRANSFORM_SINE
+        r = head.run(args.path, flush, 20, 3, peaks, peak_src, transform=other)
+        wl[("real_even_transform_" if other == leg.TRANSFORM_REG else "sine_form_") + name] = strip(r)
         del head
         # the B=4096, K=1025 workload: split, plain FP32, FP64, collapsed
         c2name = "cheb_b4096_k1025_n512_m2048"

@@ -31,22 +31,28 @@ def free_bytes():
     return torch.cuda.mem_get_info()[0]
 
 
+def settle(leg):
+    """Collect the plans and batches earlier tests left to the garbage
+    collector (their memory returns to the device), then the library's count."""
+    import gc
+    gc.collect()
+    torch.cuda.synchronize()
+    return leg.memory_info()
+
+
 def sweep(leg, monkeypatch, attempt, max_k=100):
     """attempt() under LEG_FAULT_ALLOC = 1, 2, ... until it succeeds; returns
     (number of allocations the call makes, the successful result).  After
     every failed attempt the library holds exactly what it held before."""
-    import gc
-    gc.collect()   # plans other tests left to the collector release their memory now
+    held = settle(leg)
     base = free_bytes()
-    held = leg.memory_info()
     for k in range(1, max_k):
         monkeypatch.setenv("LEG_FAULT_ALLOC", str(k))
         try:
             obj = attempt()
         except leg.LegError as e:
             assert e.code == 2, (k, str(e))   # LEG_ERR_OOM
-            gc.collect()
-            assert leg.memory_info() == held, (k, held, leg.memory_info())
+            assert settle(leg) == held, (k, held, leg.memory_info())
             assert abs(free_bytes() - base) <= SLACK, (k, base - free_bytes())
             continue
         monkeypatch.delenv("LEG_FAULT_ALLOC")
@@ -59,19 +65,16 @@ def sweep(leg, monkeypatch, attempt, max_k=100):
 def test_plan_create_fails_cleanly(leg, monkeypatch, dtype_name, flags):
     dt = getattr(leg, dtype_name)
     leg.Plan(64, 256, 65, 0, dt, flags=flags).close()   # loads the kernels once
-    import gc
-    gc.collect()
+    held = settle(leg)
     base = free_bytes()
-    held = leg.memory_info()
     n, plan = sweep(leg, monkeypatch, lambda: leg.Plan(64, 256, 65, 0, dt, flags=flags))
     assert n >= 3
     plan.close()
     assert leg.memory_info() == held
     assert abs(free_bytes() - base) <= SLACK
     like = leg.Plan(64, 256, 65, 0, leg.F64)
-    gc.collect()
+    held = settle(leg)
     base = free_bytes()
-    held = leg.memory_info()
     n, p2 = sweep(leg, monkeypatch, lambda: leg.Plan.like(like, dt))
     assert n >= 2
     p2.close()
@@ -107,6 +110,7 @@ def test_forward_host_fails_cleanly(leg, monkeypatch):
     f_host = torch.from_numpy(f_np)            # pageable: the staged path allocates device copies
     c_host = torch.empty((B, N), dtype=torch.float32)
     plan2 = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    plan2.reserve(B)   # the plan's own workspace first: the sweep covers the call's device copies
     n, _ = sweep(leg, monkeypatch, lambda: plan2.forward_host(f_host, c_host))
     assert n >= 1
     assert torch.equal(c_host, ref)
@@ -116,6 +120,7 @@ def test_plain_method_scratch_fails_cleanly(leg, monkeypatch):
     # an FP32 plan's G holds 4-byte values: the FP64 plain method takes a
     # stream-ordered allocation for its G (after the plan's workspace)
     plan = leg.Plan(64, 256, 17, 32, leg.F32)
+    plan.reserve(2)   # the plan's own workspace first: the sweep covers the call's G
     params = torch.tensor([0.5, 0.3], dtype=torch.float64, device="cuda")
     ref = leg.Plan(64, 256, 17, 32, leg.F64).plain_forward(leg.FAMILY_GENFN, params)
     n, c = sweep(leg, monkeypatch, lambda: plan.plain_forward(leg.FAMILY_GENFN, params))
@@ -136,8 +141,7 @@ def test_ragged_fails_cleanly(leg, monkeypatch):
                   coef_off=dev(lay["coef_off"], torch.int64))
     ref = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
     leg.Ragged(plans, lay["bidx"], n, lay["in_off"], lay["out_off"]).forward(f, ref)
-    torch.cuda.synchronize()
-    held = leg.memory_info()
+    held = settle(leg)
     k, batch = sweep(leg, monkeypatch, lambda: leg.Ragged(plans, lay["bidx"], n, lay["in_off"], lay["out_off"]))
     assert k >= 3 * len(lay["buckets"])
     c = torch.empty_like(ref)
@@ -145,7 +149,7 @@ def test_ragged_fails_cleanly(leg, monkeypatch):
     torch.cuda.synchronize()
     assert torch.equal(c, ref)
     batch.close()
-    assert leg.memory_info() == held
+    assert settle(leg) == held
     # the one-call form: its cached batch is built inside the call
     arrays = (dev(lay["bidx"], torch.int32), dev(n, torch.int32), dev(lay["in_off"], torch.int64),
               dev(lay["out_off"], torch.int64))
@@ -157,5 +161,5 @@ def test_ragged_fails_cleanly(leg, monkeypatch):
     assert leg.memory_info() != held       # the cached one-call batch
     for p in plans:                         # destroying a plan drops the cached batches that use it
         p.close()
-    n_after, _ = leg.memory_info()
+    n_after, _ = settle(leg)
     assert n_after < held[0]
