@@ -69,6 +69,8 @@ def parse():
                          "skips the autotuner")
     ap.add_argument("--transform", default=None, choices=["reg", "stockham", "sine"],
                     help="transform kernel of the headline plan")
+    ap.add_argument("--radix", type=int, default=0, choices=[0, 8, 16],
+                    help="radix of the register-tiled transform passes (with --tile and --transform)")
     return ap.parse_args()
 
 
@@ -541,7 +543,7 @@ def table1_plain(leg, torch, O):
     return out
 
 
-def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3):
+def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3, tile=None, transform=None):
     """The ragged workload: 10,000 closed-form functions in 9 size buckets,
     one grouped persistent GEMM launch, replayed as a CUDA graph."""
     cfg = workloads.CONFIGS["ragged_10000"]
@@ -550,9 +552,21 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
     lay = workloads.ragged_layout(fam, par, n, rng)
     t0 = time.time()
     plans = [leg.Plan(*workloads.bucket_sizes(Nb), dtype=leg.SPLIT_FP16) for Nb in lay["buckets"]]
-    batch = leg.Ragged(plans, lay["bidx"], n, lay["in_off"], lay["out_off"])
     torch.cuda.synchronize()
     setup = time.time() - t0
+    # each bucket's transform (kernel and radix) timed on a batch of its size,
+    # before the batch captures its launches
+    tr = {}
+    for b, (Nb, p) in enumerate(zip(lay["buckets"], plans)):
+        if transform is not None:   # fixed from the command line
+            if p.M >= 256 or transform[0] != leg.TRANSFORM_SINE:
+                p.set_transform(*transform)
+        else:
+            Bb = int(np.sum(lay["bidx"] == b))
+            p.autotune(torch.randn((Bb, p.K), dtype=torch.float32, device="cuda"))
+        tr[str(Nb)] = "%s, radix %d" % (["real-even", "Stockham", "sine form"][p.transform], p.transform_radix)
+    batch = leg.Ragged(plans, lay["bidx"], n, lay["in_off"], lay["out_off"])
+    torch.cuda.synchronize()
     dev = lambda a, dt: torch.tensor(a, dtype=dt, device="cuda")
     f = torch.empty(lay["n_in"], dtype=torch.float32, device="cuda")
     leg.sample_cl(dev(fam, torch.int32), dev(par, torch.float64), dev(lay["K"], torch.int32),
@@ -560,7 +574,11 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
                   coef_off=dev(lay["coef_off"], torch.int64))
     c = torch.empty(lay["n_out"], dtype=torch.float32, device="cuda")
     model_tn = batch.tile_info()["tn"]
-    tuned_tn = batch.autotune(f, c)   # the grouped launch's tile width, timed on this batch
+    if tile is not None:
+        batch.set_tile(tile)
+        tuned_tn = batch.tile_info()["tn"]
+    else:
+        tuned_tn = batch.autotune(f, c)   # the grouped launch's tile width, timed on this batch
     ts, _ = time_steps(torch, lambda: batch.forward(f, c), flush, steps, warmup)
     st = []
     for _ in range(min(5, steps)):
@@ -592,6 +610,7 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
            "stages_ms": {"input_split": split_ms, "grouped_gemm": gemm_ms, "transforms": fft_ms},
            "roofline": roof, "tile_width": tuned_tn, "tile_width_cost_model": model_tn,
            "tile_chosen_by": "leg_ragged_autotune (timed candidates: the cost model's width and 128..64)",
+           "bucket_transforms": tr,
            "gpu_launches_per_step": 2 + len(lay["buckets"]), "cuda_graph": True}
     if with_ref:
         from oracle import oracle as O
@@ -695,7 +714,12 @@ def whole_job_rate(world: int, units_per_rank: int, ms_per_step: float) -> float
 
 def ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
     """--workload ragged_10000: the ragged batch as the timed workload."""
-    r = ragged(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup)
+    fixed = None
+    if args.transform is not None:
+        fixed = ({"reg": leg.TRANSFORM_REG, "stockham": leg.TRANSFORM_STOCKHAM, "sine": leg.TRANSFORM_SINE}[
+            args.transform], args.radix)
+    r = ragged(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup,
+               tile=args.tile, transform=fixed)
     ms = max_over_ranks(torch, dist, r["ms_per_step"], "cuda")
     if rank == 0:
         line = {"metric": METRIC, "value": whole_job_rate(world, r["coefficients"], ms), "unit": UNIT,
@@ -705,7 +729,8 @@ def ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
                 "config": {"workload": "ragged_10000", "functions": r["functions"], "buckets": r["buckets"],
                            "l2": "flushed (512 MiB write) before every timed step"},
                 "max_rel_err": r.get("max_rel_err"), "err_sample": r.get("err_sample"), "roofline": r["roofline"],
-                "stages_ms": r["stages_ms"], "gpu_launches": r["gpu_launches_per_step"] * args.steps}
+                "stages_ms": r["stages_ms"], "tile_width": r["tile_width"], "bucket_transforms": r["bucket_transforms"],
+                "gpu_launches": r["gpu_launches_per_step"] * args.steps}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.barrier()
@@ -744,6 +769,8 @@ def gpu_arm(args, rank, world, local_rank):
         plan.set_transform({"reg": leg.TRANSFORM_REG, "stockham": leg.TRANSFORM_STOCKHAM,
                             "sine": leg.TRANSFORM_SINE}[args.transform])
         tuned = {"tn": args.tile, "fft": plan.transform, "source": "command line"}
+        if args.radix:
+            plan.set_transform(plan.transform, args.radix)
         if args.path == "split_fp16":
             head.retile()
     else:
@@ -794,7 +821,9 @@ def gpu_arm(args, rank, world, local_rank):
         "config": {"workload": name, "B": B, "K": head.K, "N": N, "M": head.M, "Q": (head.K + 1) // 2,
                    "path": args.path, "tile_width": head.tn,
                    "launch_settings": {"tile_width_setting": tuned["tn"],
-                                       "transform": TRANSFORM_NAMES[tuned["fft"]], "chosen_by": tuned["source"]},
+                                       "transform": TRANSFORM_NAMES[tuned["fft"]],
+                                       "transform_radix": head.plan(args.path).transform_radix,
+                                       "chosen_by": tuned["source"]},
                    "l2": "flushed (512 MiB write) before every timed step; the operator planes (%.0f MB) also "
                          "exceed L2" % (3 * (head.rows - 1) * head.Kp * 2 / 1e6),
                    "inputs": "random decaying Chebyshev series sampled at CL nodes, FP32, seeded"},

@@ -281,7 +281,10 @@ LEG_API int leg_forward_ragged(const leg_plan_t *plans, int nplans, int count, c
  * persistent tcgen05 launch over the Abel-GEMM tiles of all buckets, one
  * transform launch per bucket writing the packed output (the transforms of
  * the buckets run concurrently on the batch's internal streams; each uses its
- * plan's transform kernel, see leg_plan_set_transform).  The first call runs
+ * plan's transform kernel, see leg_plan_set_transform, as set when the
+ * batch's launches are captured on its second call: later changes to the
+ * plans reach the batch through a new batch, or the new graph that
+ * leg_ragged_set_tile causes).  The first call runs
  * the sequence directly; later calls replay it as a CUDA graph (captured
  * again when f_packed, c_packed or the tile width change).  When `stream` is
  * itself being captured, the launches join the caller's graph instead.
@@ -364,16 +367,18 @@ LEG_API int leg_plan_set_tile(leg_plan_t plan, int tn);
 
 /*
  * leg_plan_set_transform -- the kernel of the plan's forward transform stage:
- * LEG_TRANSFORM_REG (the default), LEG_TRANSFORM_STOCKHAM or
+ * variant LEG_TRANSFORM_REG (the default), LEG_TRANSFORM_STOCKHAM or
  * LEG_TRANSFORM_SINE (the sine form of Eq. 2.13, see LEG_FLAG_SINE_FORM;
- * M >= 256, else LEG_ERR_UNSUPPORTED).  All three compute the same linear
- * map; results differ by rounding.  The plain method (leg_plain_forward*) and
+ * M >= 256, else LEG_ERR_UNSUPPORTED), and the radix of the register-tiled
+ * kernels' FFT passes: 8 or 16 complex values per thread (0 = the default, 8;
+ * 16 takes effect for M >= 2048).  All choices compute the same linear map;
+ * results differ by rounding.  The plain method (leg_plain_forward*) and
  * ragged batches use the plan's choice too; leg_backward always applies the
  * real-even adjoint (the transpose of that same map).
- * leg_plan_get_transform -- the current choice.
+ * leg_plan_get_transform -- the current variant and radix (either may be NULL).
  */
-LEG_API int leg_plan_set_transform(leg_plan_t plan, int variant);
-LEG_API int leg_plan_get_transform(leg_plan_t plan, int *variant);
+LEG_API int leg_plan_set_transform(leg_plan_t plan, int variant, int radix);
+LEG_API int leg_plan_get_transform(leg_plan_t plan, int *variant, int *radix);
 
 /*
  * leg_plan_tile_info -- the tile of the forward GEMM for a batch of B
@@ -385,18 +390,21 @@ LEG_API int leg_plan_tile_info(leg_plan_t plan, int B, int *tn, int *pairs, int 
 
 /*
  * leg_plan_autotune -- choose, by timing on the caller's batch, the launch
- * parameters that do not change results, and store them in the plan:
- * the tile width of the tensor-core GEMM (LEG_SPLIT_FP16, LEG_BF16: the
- * library's model choice and the multiples of 16 from the plan's maximum down
- * to 64) and the kernel of the FP64 / double-float transform (register-tiled
- * or shared-memory Stockham).  Not a step of the paper's method: a tuning aid.
+ * parameters of the plan and store them in it: the tile width of the
+ * tensor-core GEMM (LEG_SPLIT_FP16, LEG_BF16: the library's model choice and
+ * the multiples of 16 from the plan's maximum down to 64; results do not
+ * depend on it) and the forward transform (variant and radix, as
+ * leg_plan_set_transform; the candidates compute the same map and differ by
+ * rounding; plans created with LEG_FLAG_SINE_FORM keep the sine form and tune
+ * its radix).  Not a step of the paper's method: a tuning aid.
  *   f  device, B x K input (as leg_forward);  c  device, B x N output buffer
  *      (overwritten).  Synchronises the stream; runs each candidate four times.
  *   *tn, *fft (either may be NULL): the chosen tile width (0 = the model's
- *      choice per call) and transform kernel (0 register-tiled, 1 Stockham).
+ *      choice per call) and transform variant (LEG_TRANSFORM_*; its radix:
+ *      leg_plan_get_transform).
  * With the environment variable LEG_TUNE_CACHE naming a file, choices are
- * appended there keyed by (device name, dtype, N, M, K, Q, B) and reused
- * without timing by later calls with the same key.
+ * appended there keyed by (device name, dtype, N, M, K, Q, flags, B) and
+ * reused without timing by later calls with the same key.
  */
 LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream, int *tn,
                               int *fft);

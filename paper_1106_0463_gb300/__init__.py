@@ -81,8 +81,8 @@ def _load():
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
-        "leg_plan_set_transform": ([vp, i], i),
-        "leg_plan_get_transform": ([vp, ctypes.POINTER(i)], i),
+        "leg_plan_set_transform": ([vp, i, i], i),
+        "leg_plan_get_transform": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_tile_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_ragged_create": ([ctypes.POINTER(vp), ctypes.POINTER(vp), i, i, vp, vp, vp, vp], i),
@@ -221,16 +221,24 @@ class Plan:
         """Functions per CTA-pair tile of the tensor-core GEMM (0 = automatic)."""
         _check(_lib.leg_plan_set_tile(self._h, int(tn)))
 
-    def set_transform(self, variant: int):
+    def set_transform(self, variant: int, radix: int = 0):
         """Kernel of the forward transform stage: TRANSFORM_REG, TRANSFORM_STOCKHAM
-        or TRANSFORM_SINE (leg_plan_set_transform); same map, rounding differs."""
-        _check(_lib.leg_plan_set_transform(self._h, int(variant)))
+        or TRANSFORM_SINE, and the radix (8 or 16 values per thread; 0 = 8) of
+        the register-tiled kernels (leg_plan_set_transform); same map, rounding
+        differs."""
+        _check(_lib.leg_plan_set_transform(self._h, int(variant), int(radix)))
 
     @property
     def transform(self) -> int:
         v = ctypes.c_int()
-        _check(_lib.leg_plan_get_transform(self._h, ctypes.byref(v)))
+        _check(_lib.leg_plan_get_transform(self._h, ctypes.byref(v), None))
         return v.value
+
+    @property
+    def transform_radix(self) -> int:
+        r = ctypes.c_int()
+        _check(_lib.leg_plan_get_transform(self._h, None, ctypes.byref(r)))
+        return r.value
 
     def autotune(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> dict:
         """leg_plan_autotune: time the GEMM tile widths and the transform

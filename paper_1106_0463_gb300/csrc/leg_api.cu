@@ -435,6 +435,7 @@ extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStre
     key.Fh = p->Fh;
     key.tn = p->tn;
     key.fft = p->fft_variant;
+    key.fft_log2e = p->fft_log2e;
     key.wait = p->wait_limit;
     if (p->fwd_exec && key == p->fwd_key) {
         LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
@@ -606,21 +607,25 @@ extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
     return LEG_OK;
 }
 
-extern "C" int leg_plan_set_transform(leg_plan_t p, int variant)
+extern "C" int leg_plan_set_transform(leg_plan_t p, int variant, int radix)
 {
     if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
     if (variant < LEG_TRANSFORM_REG || variant > LEG_TRANSFORM_SINE)
         return leg_set_error(LEG_ERR_INVALID_ARG, "unknown transform variant");
+    if (radix != 0 && radix != 8 && radix != 16)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "radix must be 0 (default), 8 or 16");
     if (variant == LEG_TRANSFORM_SINE && p->M < LEG_TRANSFORM_MIN_M_REG)
         return leg_set_error(LEG_ERR_UNSUPPORTED, "the sine-form transform needs M >= 256");
     p->fft_variant = variant;
+    p->fft_log2e = (radix == 16) ? 4 : 3;
     return LEG_OK;
 }
 
-extern "C" int leg_plan_get_transform(leg_plan_t p, int *variant)
+extern "C" int leg_plan_get_transform(leg_plan_t p, int *variant, int *radix)
 {
-    if (!p || !variant) return leg_set_error(LEG_ERR_INVALID_ARG, "null plan or variant");
-    *variant = p->fft_variant;
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (variant) *variant = p->fft_variant;
+    if (radix) *radix = 1 << p->fft_log2e;
     return LEG_OK;
 }
 

@@ -21,11 +21,11 @@ namespace {
 // converted to the arithmetic type), left in Xs[D::px(n)], n = 0..L (a real
 // view of buf).  Only X_0..X_{2 kmax + 1} and X_L are exact: the
 // recombination skips k > kmax (kmax = H - 1 for all of them).
-template <class R, int LOG2H, class Load>
+template <class R, int LOG2H, int XE, class Load>
 __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int t, const typename Ar<R>::TW *tw,
                                       int kmax, Load load)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     using T_ = typename F::T;
     constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
@@ -49,11 +49,11 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
         }
         v[b] = {F::norm(yy[0]), F::norm(yy[1])};
     }
-    const T_ x1 = F::norm(F::add(F::sub(load(0), load(L)), F::pow2(fn_sum<R, LOG2H>(part, t, wsum), 1)));
+    const T_ x1 = F::norm(F::add(F::sub(load(0), load(L)), F::pow2(fn_sum<R, LOG2H, XE>(part, t, wsum), 1)));
     fsync<T>();   // load() may read buf (the staged row): all reads precede the first pass's writes
 
     // 2. FFT of length H
-    fft16<R, LOG2H>(v, buf, t, tw);
+    fft16<R, LOG2H, XE>(v, buf, t, tw);
     fsync<T>();
 
     // 3. recombination for k = t + i T: 2 Re Y_k (= X_2k) and 2 Im Y_k
@@ -96,7 +96,7 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
         run = F::add(run, Xs[D::px(2 * (t * E + i) + 1)]);
         iy[i] = run;
     }
-    const T_ incl = fn_scan<R, LOG2H>(run, t, wsum);
+    const T_ incl = fn_scan<R, LOG2H, XE>(run, t, wsum);
     const T_ offs = F::add(x1, F::sub(incl, run));   // X_1 + exclusive prefix
 #pragma unroll
     for (int i = 0; i < E; ++i) Xs[D::px(2 * (t * E + i) + 1)] = F::norm(F::add(offs, iy[i]));
@@ -104,28 +104,28 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
 }
 
 
-template <class R, int LOG2H>
-__global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dct16_forward_kernel(
+template <class R, int LOG2H, int XE>
+__global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE>()) dct16_forward_kernel(
     const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
     const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
     const int *__restrict__ n_out)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     using T_ = typename F::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
-    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
-    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * gslots<R, LOG2H>()) + grp * D::WARPS;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H, XE>();
+    T_ *wsum = reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) + D::FPB * gslots<R, LOG2H, XE>()) + grp * D::WARPS;
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
     using GT = typename Ar<R>::GT;
-    stage_row<R, LOG2H>(buf, G, ldg, f, t);
+    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t);
     const GT *g = reinterpret_cast<const GT *>(buf);
     // c_n for n < N reads X_0..X_N: X_2k for k <= N/2 and X_2k+1 for k <= (N-1)/2
     const int kmax = min(D::H - 1, N / 2);
-    dct16<R, LOG2H>(buf, wsum, t, tw, kmax, [&](int j) -> T_ { return GIn<R>::get(g, j); });
+    dct16<R, LOG2H, XE>(buf, wsum, t, tw, kmax, [&](int j) -> T_ { return GIn<R>::get(g, j); });
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
     typename Ar<R>::OUT *cf = c + (size_t)f * N;
@@ -167,7 +167,7 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
         if (n >= 1) x = F::sub(x, F::mul(F::of_int(2 * n - 1), in_of<R>(vf[n - 1])));
         return x;
     };
-    dct16<R, LOG2H>(buf, wsum, t, tw, D::H - 1, load);
+    dct16<R, LOG2H, LEG_DCT16_LOG2E>(buf, wsum, t, tw, D::H - 1, load);
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
     const T_ x0 = load(0), xL = load(L);
@@ -178,13 +178,13 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
     }
 }
 
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE>
 int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
                const long long *out_off, const int *n_out)
 {
-    using D = D16<LOG2H>;
-    auto kern = dct16_forward_kernel<R, LOG2H>;
-    const size_t smem = d16_smem<R, LOG2H>();
+    using D = D16<LOG2H, XE>;
+    auto kern = dct16_forward_kernel<R, LOG2H, XE>;
+    const size_t smem = d16_smem<R, LOG2H, XE>();
     LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (B + D::FPB - 1) / D::FPB;
     // programmatic dependent launch: CTAs start on SMs the GEMM has left
@@ -220,14 +220,20 @@ int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw,
 }
 
 template <class R, int LO, int HI>
-int dispatch_fwd(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
                  const int *rowfn, const long long *out_off, const int *n_out)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
     } else {
-        if (lg == LO) return launch_fwd<R, LO>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
-        return dispatch_fwd<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        if (lg == LO) {
+            // radix 16 differs from radix 8 only from H = 512 on (at least 32 threads of 16 values)
+            if constexpr (LO >= 9) {
+                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+            }
+            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        }
+        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }
 
@@ -244,12 +250,14 @@ int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const
 
 }  // namespace
 
-// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768).
-int leg_dct16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
-                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
+// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768); at most
+// 2^log2e values per thread (3: radix-8 passes, 4: radix-16).
+int leg_dct16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
 {
-    if (dtype == LEG_F64) return dispatch_fwd<double, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
-    return dispatch_fwd<dfl, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    if (dtype == LEG_F64)
+        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
 }
 
 int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,

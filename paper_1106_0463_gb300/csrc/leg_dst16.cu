@@ -34,10 +34,10 @@ namespace {
 
 // zeta = FFT_H(Y) of the row delivered by load(j), j = 0..L (the caller's
 // element type converted to the arithmetic type), left in buf[D::pc(m)].
-template <class R, int LOG2H, class Load>
+template <class R, int LOG2H, int XE, class Load>
 __device__ __forceinline__ void dst16(CxT<R> *buf, int t, const typename Ar<R>::TW *tw, Load load)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     using T_ = typename F::T;
     constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
@@ -67,31 +67,31 @@ __device__ __forceinline__ void dst16(CxT<R> *buf, int t, const typename Ar<R>::
     }
     fsync<T>();   // load() reads buf (the staged row): all reads precede the first pass's writes
     // 2. FFT of length H
-    fft16<R, LOG2H>(v, buf, t, tw);
+    fft16<R, LOG2H, XE>(v, buf, t, tw);
     fsync<T>();
 }
 
 // c[f, n] = (-1)^n (2n+1) z_{i(n)} / M, n < N (or, with rowfn, the first
 // n_out coefficients of function rowfn[f] at c + out_off[.]).
-template <class R, int LOG2H>
-__global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dst16_forward_kernel(
+template <class R, int LOG2H, int XE>
+__global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE>()) dst16_forward_kernel(
     const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
     const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
     const int *__restrict__ n_out)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     using T_ = typename F::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int grp = threadIdx.x / D::T, t = threadIdx.x % D::T;
-    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H, XE>();
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);   // tail groups recompute the last function
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
     using GT = typename Ar<R>::GT;
-    stage_row<R, LOG2H>(buf, G, ldg, f, t);
+    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t);
     const GT *g = reinterpret_cast<const GT *>(buf);
-    dst16<R, LOG2H>(buf, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
+    dst16<R, LOG2H, XE>(buf, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
     if (!live) return;
     typename Ar<R>::OUT *cf = c + (size_t)f * N;
     int nn = N;
@@ -111,13 +111,13 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, fwd_minb<R, LOG2H>()) dst
     }
 }
 
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE>
 int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
                const long long *out_off, const int *n_out)
 {
-    using D = D16<LOG2H>;
-    auto kern = dst16_forward_kernel<R, LOG2H>;
-    const size_t smem = d16_smem<R, LOG2H>();
+    using D = D16<LOG2H, XE>;
+    auto kern = dst16_forward_kernel<R, LOG2H, XE>;
+    const size_t smem = d16_smem<R, LOG2H, XE>();
     LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (B + D::FPB - 1) / D::FPB;
     // programmatic dependent launch, as the real-even transform
@@ -138,29 +138,39 @@ int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cu
 }
 
 template <class R, int LO, int HI>
-int dispatch_fwd(int lg, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
+int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
                  const int *rowfn, const long long *out_off, const int *n_out)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
     } else {
-        if (lg == LO) return launch_fwd<R, LO>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
-        return dispatch_fwd<R, LO + 1, HI>(lg, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        if (lg == LO) {
+            // radix 16 differs from radix 8 only from H = 512 on (at least 32 threads of 16 values)
+            if constexpr (LO >= 9) {
+                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+            }
+            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+        }
+        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }
 
 }  // namespace
 
-// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768).  dtype
+// H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768); at most
+// 2^log2e values per thread (3: radix-8 passes, 4: radix-16).  dtype
 // LEG_F64: FP64 G and c, table of double2; LEG_SPLIT_FP16: double-float G
 // (float2), FP32 c, table of float4; LEG_F32 / LEG_BF16: FP32 G and c,
 // table of float2.
-int leg_dst16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
-                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
+int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
 {
     switch (dtype) {
-    case LEG_F64: return dispatch_fwd<double, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
-    case LEG_SPLIT_FP16: return dispatch_fwd<dfl, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
-    default: return dispatch_fwd<float, 6, 13>(log2h, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    case LEG_F64:
+        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    case LEG_SPLIT_FP16:
+        return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    default:
+        return dispatch_fwd<float, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }

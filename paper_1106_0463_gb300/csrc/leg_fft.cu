@@ -581,20 +581,22 @@ int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, c
     if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H) {
         const void *tw = p->dtype == LEG_F64 ? (const void *)p->tw64
                          : p->dtype == LEG_SPLIT_FP16 ? (const void *)p->twdf : (const void *)p->tw32;
-        return leg_dst16_forward(p->dtype, lg - 1, G, ldg, c, p->N, B, tw, st, nullptr, nullptr, nullptr);
+        return leg_dst16_forward(p->dtype, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, tw, st, nullptr, nullptr,
+                                 nullptr);
     }
     switch (p->dtype) {
     case LEG_F64:
         if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
-            return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
+            return leg_dct16_forward(LEG_F64, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->tw64, st, nullptr,
+                                     nullptr, nullptr);
         return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
         return dispatch_forward<float, 2, 14>(lg, G, ldg, c, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
         if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
-            return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c, p->N, B, p->twdf, st, nullptr, nullptr,
-                                     nullptr);
+            return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->twdf, st,
+                                     nullptr, nullptr, nullptr);
         return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->twdf, st);
     }
     return leg_set_error(LEG_ERR_INVALID_ARG, "bad dtype");
@@ -626,9 +628,11 @@ int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, 
     if (B == 0) return LEG_OK;
     const int lg = ilog2(p->L);
     if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
-        return leg_dst16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
+        return leg_dst16_forward(LEG_F64, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr,
+                                 nullptr);
     if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
-        return leg_dct16_forward(LEG_F64, lg - 1, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr, nullptr);
+        return leg_dct16_forward(LEG_F64, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->tw64, st, nullptr, nullptr,
+                                 nullptr);
     return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
 }
 
@@ -641,10 +645,10 @@ int leg_fft_forward_ragged(const leg_plan *p, const void *G, int ldg, float *c_p
     if (p->dtype != LEG_SPLIT_FP16) return leg_set_error(LEG_ERR_UNSUPPORTED, "ragged batches need split plans");
     const int lg = ilog2(p->L);
     if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
-        return leg_dst16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off,
-                                 n_out);
+        return leg_dst16_forward(LEG_SPLIT_FP16, lg - 1, p->fft_log2e, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn,
+                                 out_off, n_out);
     if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
-        return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off,
-                                 n_out);
+        return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, p->fft_log2e, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn,
+                                 out_off, n_out);
     return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c_packed, p->N, B, p->twdf, st, rowfn, out_off, n_out);
 }

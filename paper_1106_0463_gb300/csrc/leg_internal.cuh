@@ -110,6 +110,7 @@ struct leg_plan {
     double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
     int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
     int fft_variant = 0;      // LEG_TRANSFORM_*: the forward transform kernel (same map, rounding differs)
+    int fft_log2e = 3;        // register-tiled forward transforms: 2^fft_log2e values per thread (radix 8 or 16)
     bool collapsed() const { return (flags & LEG_FLAG_COLLAPSED) != 0; }
     // transposed split planes for the adjoint GEMM: K x Kpr (Kpr = rows padded),
     // each column k of the operator scaled by its own power of two
@@ -143,12 +144,12 @@ struct leg_plan {
         void *c = nullptr;
         int B = 0, wsB = 0;   // wsB: the workspace's capacity (plane strides depend on it)
         void *G = nullptr, *Fh = nullptr;
-        int tn = 0, fft = 0;
+        int tn = 0, fft = 0, fft_log2e = 0;
         long long wait = 0;
         bool operator==(const GraphKey &o) const
         {
             return f == o.f && c == o.c && B == o.B && wsB == o.wsB && G == o.G && Fh == o.Fh && tn == o.tn &&
-                   fft == o.fft && wait == o.wait;
+                   fft == o.fft && fft_log2e == o.fft_log2e && wait == o.wait;
         }
     };
     GraphKey fwd_key;
@@ -267,14 +268,15 @@ constexpr int LEG_TRANSFORM_MIN_M_REG = 256;   // smallest M of the register-til
 
 // register-tiled transforms (leg_dct16.cu), H = 2^log2h with 6 <= log2h <= 13;
 // dtype LEG_F64 (FP64 G, c) or LEG_SPLIT_FP16 (double-float G, FP32 c)
-int leg_dct16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
-                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
+// log2e: at most 2^log2e values per thread (3 or 4: radix-8 or radix-16 passes)
+int leg_dct16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
                       cudaStream_t st);
 // register-tiled sine form (leg_dst16.cu), same H range; dtype LEG_F64,
 // LEG_SPLIT_FP16 (double-float G, FP32 c) or LEG_F32 / LEG_BF16 (FP32)
-int leg_dst16_forward(int dtype, int log2h, const void *G, int ldg, void *c, int N, int B, const void *tw,
-                      cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
+int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,

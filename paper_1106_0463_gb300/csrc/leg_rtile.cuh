@@ -207,11 +207,13 @@ __device__ __forceinline__ void dft(CxT<R> (&x)[P])
 #endif
 
 
-template <int LOG2H> struct D16 {
+// Shape of a register-tiled transform of length H = 2^LOG2H with at most 2^XE
+// complex values per thread (XE = 3: radix-8 passes, 4: radix-16).
+template <int LOG2H, int XE = LEG_DCT16_LOG2E> struct D16 {
     static constexpr int H = 1 << LOG2H;
     static constexpr int L = 2 * H;
     static constexpr int M = 2 * L;
-    static constexpr int LOG2E = (LOG2H - 5 < LEG_DCT16_LOG2E) ? LOG2H - 5 : LEG_DCT16_LOG2E;
+    static constexpr int LOG2E = (LOG2H - 5 < XE) ? LOG2H - 5 : XE;
     static constexpr int E = 1 << LOG2E;
     static constexpr int T = H / E;                                 // threads per function, >= 32
     static constexpr int FPB = (T >= 128) ? 1 : 128 / T;            // functions per CTA
@@ -222,7 +224,9 @@ template <int LOG2H> struct D16 {
     // resident CTAs per SM asked of the register allocator: about 24-32 warps
     // per SM (80 registers at 128 and 256 threads, 64 at 512; 158 and 128
     // registers without the target left one CTA per SM)
-    static constexpr int MINB = THREADS <= 128 ? 6 : THREADS == 256 ? 3 : THREADS == 512 ? 2 : 1;
+    // radix-16 threads hold twice the values: a 128-register budget
+    static constexpr int MINB = XE >= 4 ? (THREADS >= 512 ? 1 : 512 / THREADS)
+                                        : THREADS <= 128 ? 6 : THREADS == 256 ? 3 : THREADS == 512 ? 2 : 1;
     static constexpr int SLOTS = H + H / E + 1;                     // padded complex slots per function
     static constexpr int WARPS = T / 32;
     // FFT buffer: one padding slot per E complex values; real view (X): one
@@ -236,10 +240,10 @@ template <int LOG2H> struct D16 {
 // arithmetic type R: D16::SLOTS, rounded up so that every buffer starts on a
 // 16-byte boundary (the row staging copies 16 bytes at a time).  SLOTS is odd,
 // so 8-byte complex values (FP32) take one more slot; 16-byte ones keep SLOTS.
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 __host__ __device__ constexpr int gslots()
 {
-    constexpr int S = D16<LOG2H>::SLOTS;
+    constexpr int S = D16<LOG2H, XE>::SLOTS;
     return (S * (int)sizeof(CxT<R>)) % 16 == 0 ? S : S + (16 / (int)sizeof(CxT<R>)) - 1;
 }
 
@@ -273,11 +277,11 @@ __device__ __forceinline__ void twid(const float4 *tw, int i, dfl &c, dfl &s)
 // One Stockham pass of radix P over v = x[t + b T] (b < E): butterflies
 // j = t + bb T (bb < E/P) of stride Ns, twiddles e^{2 pi i r k / (P Ns)},
 // outputs to buf[D::pc((j - k) P + k + r Ns)].
-template <class R, int LOG2H, int P, int LOGP>
-__device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, int t, int Ns,
+template <class R, int LOG2H, int P, int LOGP, int XE = LEG_DCT16_LOG2E>
+__device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> *buf, int t, int Ns,
                                          const typename Ar<R>::TW *tw)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     constexpr int E = D::E, T = D::T, NB = E / P;
     const int tstep = D::M / (P * Ns);
@@ -306,20 +310,20 @@ __device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf
     }
 }
 
-template <class R, int LOG2H>
-__device__ __forceinline__ void fft_pass_any(int P, CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, int t, int Ns,
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
+__device__ __forceinline__ void fft_pass_any(int P, CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> *buf, int t, int Ns,
                                              const typename Ar<R>::TW *tw)
 {
-    if constexpr (D16<LOG2H>::E >= 16) {
-        if (P == 16) return fft_pass<R, LOG2H, 16, 4>(v, buf, t, Ns, tw);
+    if constexpr (D16<LOG2H, XE>::E >= 16) {
+        if (P == 16) return fft_pass<R, LOG2H, 16, 4, XE>(v, buf, t, Ns, tw);
     }
-    if constexpr (D16<LOG2H>::E >= 8) {
-        if (P == 8) return fft_pass<R, LOG2H, 8, 3>(v, buf, t, Ns, tw);
+    if constexpr (D16<LOG2H, XE>::E >= 8) {
+        if (P == 8) return fft_pass<R, LOG2H, 8, 3, XE>(v, buf, t, Ns, tw);
     }
-    if constexpr (D16<LOG2H>::E >= 4) {
-        if (P == 4) return fft_pass<R, LOG2H, 4, 2>(v, buf, t, Ns, tw);
+    if constexpr (D16<LOG2H, XE>::E >= 4) {
+        if (P == 4) return fft_pass<R, LOG2H, 4, 2, XE>(v, buf, t, Ns, tw);
     }
-    fft_pass<R, LOG2H, 2, 1>(v, buf, t, Ns, tw);
+    fft_pass<R, LOG2H, 2, 1, XE>(v, buf, t, Ns, tw);
 }
 
 __device__ __forceinline__ double shfl_up(double v, int off) { return __shfl_up_sync(0xffffffffu, v, off); }
@@ -337,10 +341,10 @@ __device__ __forceinline__ dfl shfl_xor(dfl v, int off)
 
 // Inclusive scan of v over the T threads of a function (warp shuffles, then
 // the warp totals through shared memory).  wsum: D::WARPS slots per function.
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 __device__ __forceinline__ typename Fa<R>::T fn_scan(typename Fa<R>::T v, int t, typename Fa<R>::T *wsum)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     using T_ = typename F::T;
     const int lane = t & 31;
@@ -362,10 +366,10 @@ __device__ __forceinline__ typename Fa<R>::T fn_scan(typename Fa<R>::T v, int t,
 }
 
 // Sum of v over the T threads of a function, returned to every thread.
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 __device__ __forceinline__ typename Fa<R>::T fn_sum(typename Fa<R>::T v, int t, typename Fa<R>::T *wsum)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using F = Fa<R>;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) v = F::add(v, shfl_xor(v, off));
@@ -384,15 +388,15 @@ __device__ __forceinline__ typename Fa<R>::T fn_sum(typename Fa<R>::T v, int t, 
 // passes of radix E (the last one smaller).  The caller synchronises the
 // function's threads before the first pass if load-time reads of buf must
 // precede its writes, and after the return before reading buf.
-template <class R, int LOG2H>
-__device__ __forceinline__ void fft16(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, int t, const typename Ar<R>::TW *tw)
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
+__device__ __forceinline__ void fft16(CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> *buf, int t, const typename Ar<R>::TW *tw)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     constexpr int E = D::E, T = D::T, H = D::H;
     int Ns = 1;
     {
         constexpr int P0 = (E < H) ? E : H;
-        fft_pass_any<R, LOG2H>(P0, v, buf, t, 1, tw);
+        fft_pass_any<R, LOG2H, XE>(P0, v, buf, t, 1, tw);
         Ns = P0;
     }
     // one copy of the pass body (runtime Ns and radix): fully unrolled passes
@@ -404,7 +408,7 @@ __device__ __forceinline__ void fft16(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, i
         for (int b = 0; b < E; ++b) v[b] = buf[D::pc(t + b * T)];
         fsync<T>();
         const int P = (H / Ns < E) ? H / Ns : E;
-        fft_pass_any<R, LOG2H>(P, v, buf, t, Ns, tw);
+        fft_pass_any<R, LOG2H, XE>(P, v, buf, t, Ns, tw);
         Ns *= P;
     }
 }
@@ -413,14 +417,14 @@ __device__ __forceinline__ void fft16(CxT<R> (&v)[D16<LOG2H>::E], CxT<R> *buf, i
 // aligned with at least one padding element) in buf, which the transform's
 // first step reads before the first FFT pass overwrites it: every 16-byte
 // copy of the row is in flight at once.  Synchronises the function's threads.
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 __device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT *G, int ldg, int f, int t)
 {
-    using D = D16<LOG2H>;
+    using D = D16<LOG2H, XE>;
     using GT = typename Ar<R>::GT;
     constexpr int BYTES = ((D::L + 1) * (int)sizeof(GT) + 15) / 16 * 16;
     static_assert(BYTES <= D::SLOTS * (int)sizeof(CxT<R>), "row of G exceeds the exchange buffer");
-    static_assert((gslots<R, LOG2H>() * (int)sizeof(CxT<R>)) % 16 == 0, "exchange buffers must be 16-byte aligned");
+    static_assert((gslots<R, LOG2H, XE>() * (int)sizeof(CxT<R>)) % 16 == 0, "exchange buffers must be 16-byte aligned");
     const char *src = reinterpret_cast<const char *>(G + (size_t)f * ldg);
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
     for (int o = 16 * t; o < BYTES; o += 16 * D::T)
@@ -455,17 +459,17 @@ __device__ __forceinline__ float out_of(dfl a) { return a.hi + a.lo; }
 // The double-float forward transform up to H = 512 runs at 7 resident CTAs
 // per SM (72 registers, a 4-byte spill): 2 us faster per step than 6 at
 // M = 2048, B = 4096; the other variants spill 48-64 bytes there and keep 6.
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 constexpr int fwd_minb()
 {
-    return (std::is_same<R, dfl>::value && LOG2H <= 9) ? 7 : D16<LOG2H>::MINB;
+    return (std::is_same<R, dfl>::value && LOG2H <= 9 && XE == 3) ? 7 : D16<LOG2H, XE>::MINB;
 }
 
-template <class R, int LOG2H>
+template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 size_t d16_smem()
 {
-    using D = D16<LOG2H>;
-    return sizeof(CxT<R>) * D::FPB * gslots<R, LOG2H>() + sizeof(typename Fa<R>::T) * D::FPB * D::WARPS;
+    using D = D16<LOG2H, XE>;
+    return sizeof(CxT<R>) * D::FPB * gslots<R, LOG2H, XE>() + sizeof(typename Fa<R>::T) * D::FPB * D::WARPS;
 }
 
 }  // namespace

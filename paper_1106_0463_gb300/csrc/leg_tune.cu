@@ -6,8 +6,9 @@
 //     plan's maximum down to 64;
 //   * transform kernel of the FFT stage: the register-tiled real-even
 //     transform, the shared-memory Stockham one, or the register-tiled sine
-//     form (Eq. 2.13); plans created with LEG_FLAG_SINE_FORM keep the sine
-//     form.
+//     form (Eq. 2.13), the register-tiled ones with radix-8 or radix-16
+//     passes (8 or 16 values per thread, for H = M/4 >= 512); plans created
+//     with LEG_FLAG_SINE_FORM keep the sine form and tune its radix.
 //
 // Each candidate runs once untimed and three times timed (CUDA events around
 // the stage, on the caller's stream); the fastest median wins and is stored
@@ -22,6 +23,7 @@
 #include <algorithm>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "leg_internal.cuh"
@@ -101,20 +103,22 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
     std::lock_guard<std::mutex> lock(leg_tune_mutex());
     const char *path = getenv("LEG_TUNE_CACHE");
     const std::string key = tune_key(p, B);
-    int tn = p->tn, fft = p->fft_variant;
+    int tn = p->tn, fft = p->fft_variant | (p->fft_log2e << 4);   // cache field: variant + radix code
     const bool tc = (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16);
     const int maxtn = (p->dtype == LEG_BF16) ? 256 : 128;
     const bool sine_fixed = (p->flags & LEG_FLAG_SINE_FORM) != 0;
-    auto valid = [&](int w, int v) {
+    auto valid = [&](int w, int code) {
+        const int v = code & 15, e = code >> 4;
         const bool tn_ok = w == 0 || (tc && w >= 16 && w <= maxtn && w % 16 == 0);
-        const bool fft_ok = v >= LEG_TRANSFORM_REG && v <= LEG_TRANSFORM_SINE &&
+        const bool fft_ok = v >= LEG_TRANSFORM_REG && v <= LEG_TRANSFORM_SINE && (e == 3 || e == 4) &&
                             (v != LEG_TRANSFORM_SINE || p->M >= LEG_TRANSFORM_MIN_M_REG) &&
                             (!sine_fixed || v == LEG_TRANSFORM_SINE);
         return tn_ok && fft_ok;
     };
     if (path && *path && leg_tune_cache_lookup(path, key, &tn, &fft) && valid(tn, fft)) {
         p->tn = tn;
-        p->fft_variant = fft;
+        p->fft_variant = fft & 15;
+        p->fft_log2e = fft >> 4;
     } else {
         int rc;
         if (tc) {
@@ -136,31 +140,47 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
             }
             p->tn = best_tn;
         }
-        if (!p->collapsed() && !sine_fixed) {   // collapsed: no transform; sine form: the caller's choice
-            // FP32 plans have one real-even kernel (Stockham) besides the sine form
-            std::vector<int> cand;
-            if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) cand = {LEG_TRANSFORM_REG, LEG_TRANSFORM_STOCKHAM};
-            else cand = {LEG_TRANSFORM_REG};
-            if (p->M >= LEG_TRANSFORM_MIN_M_REG) cand.push_back(LEG_TRANSFORM_SINE);
+        if (!p->collapsed()) {   // collapsed: no transform
+            // (variant, values-per-thread exponent) candidates; FP32 plans have one
+            // real-even kernel (Stockham) besides the sine form; radix 16 only
+            // where H = M/4 >= 512 (below that both radices give the same kernel)
+            const bool r16 = p->M >= 2048;
+            std::vector<std::pair<int, int>> cand;
+            if (!sine_fixed) {
+                if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_F64) {
+                    cand.push_back({LEG_TRANSFORM_REG, 3});
+                    if (r16 && p->M >= LEG_TRANSFORM_MIN_M_REG) cand.push_back({LEG_TRANSFORM_REG, 4});
+                    cand.push_back({LEG_TRANSFORM_STOCKHAM, 3});
+                } else {
+                    cand.push_back({LEG_TRANSFORM_REG, 3});
+                }
+            }
+            if (p->M >= LEG_TRANSFORM_MIN_M_REG) {
+                cand.push_back({LEG_TRANSFORM_SINE, 3});
+                if (r16) cand.push_back({LEG_TRANSFORM_SINE, 4});
+            }
             float best = -1.0f;
-            int best_v = LEG_TRANSFORM_REG;
-            for (int v : cand) {
-                p->fft_variant = v;
+            std::pair<int, int> best_c = cand.empty() ? std::make_pair(p->fft_variant, p->fft_log2e) : cand[0];
+            for (auto cv : cand) {
+                p->fft_variant = cv.first;
+                p->fft_log2e = cv.second;
                 float t;
                 if ((rc = time_stage(p, f, c, B, st, 2, 3, &t))) {
-                    p->fft_variant = LEG_TRANSFORM_REG;
+                    p->fft_variant = sine_fixed ? LEG_TRANSFORM_SINE : LEG_TRANSFORM_REG;
+                    p->fft_log2e = 3;
                     return rc;
                 }
                 if (best < 0 || t < best * 0.99f) {   // ties stay with the earlier candidate
                     best = t;
-                    best_v = v;
+                    best_c = cv;
                 }
             }
-            p->fft_variant = best_v;
+            p->fft_variant = best_c.first;
+            p->fft_log2e = best_c.second;
         }
-        if (path && *path) leg_tune_cache_store(path, key, p->tn, p->fft_variant);
+        if (path && *path) leg_tune_cache_store(path, key, p->tn, p->fft_variant | (p->fft_log2e << 4));
     }
     if (tn_out) *tn_out = p->tn;
-    if (fft_out) *fft_out = p->fft_variant;
+    if (fft_out) *fft_out = p->fft_variant;   // the radix: leg_plan_get_transform
     return LEG_OK;
 }

@@ -105,6 +105,26 @@ def test_sine_form_equals_real_even_route(leg):
     assert np.max(np.abs(c_stk - c_reg) / scale) < 1e-12
 
 
+@pytest.mark.parametrize("M", [2048, 8192, 32768])
+def test_radix16_matches_radix8(leg, M):
+    """The register-tiled kernels with 16 values per thread (radix-16 passes)
+    compute the same map as with 8: FP64 results agree to rounding, split
+    results to far below the split path's tolerance, for both transforms."""
+    N, K, B = M // 4, 129, 7
+    f, _, _ = workloads.random_chebyshev(B, K, (0.8, 0.95), np.random.default_rng(M + 1))
+    base = leg.Plan(N, M, K, 0, leg.F64)
+    split = leg.Plan.like(base, leg.SPLIT_FP16)
+    for plan, tol in ((base, 1e-12), (split, 1e-7)):
+        for variant in (leg.TRANSFORM_REG, leg.TRANSFORM_SINE):
+            plan.set_transform(variant, 8)
+            c8 = run(leg, plan, f)
+            plan.set_transform(variant, 16)
+            assert plan.transform_radix == 16 and plan.transform == variant
+            c16 = run(leg, plan, f)
+            scale = np.max(np.abs(c8), axis=1, keepdims=True)
+            assert np.max(np.abs(c16 - c8) / scale) < tol, (plan.dtype, variant)
+
+
 def test_sine_form_plain_method_generating_function(leg):
     cfg = workloads.CONFIGS["genfn_plain_n64"]
     plan = leg.Plan(cfg["N"], cfg["M"], 17, cfg["Q"], leg.F64, flags=leg.FLAG_SINE_FORM)
@@ -178,3 +198,5 @@ def test_sine_form_argument_checks(leg):
         p.set_transform(leg.TRANSFORM_SINE)
     with pytest.raises(leg.LegError):
         p.set_transform(7)
+    with pytest.raises(leg.LegError):
+        p.set_transform(leg.TRANSFORM_REG, 32)
