@@ -71,8 +71,6 @@ def parse():
                     help="transform kernel of the headline plan")
     ap.add_argument("--radix", type=int, default=0, choices=[0, 8, 16],
                     help="radix of the register-tiled transform passes (with --tile and --transform)")
-    ap.add_argument("--ksplit", default="auto", choices=["auto", "off", "on"],
-                    help="work sharing of the split GEMM (with --tile and --transform)")
     return ap.parse_args()
 
 
@@ -774,8 +772,6 @@ def gpu_arm(args, rank, world, local_rank):
         if args.radix:
             plan.set_transform(plan.transform, args.radix)
         if args.path == "split_fp16":
-            plan.set_ksplit({"auto": leg.KSPLIT_AUTO, "off": leg.KSPLIT_OFF, "on": leg.KSPLIT_ON}[args.ksplit])
-        if args.path == "split_fp16":
             head.retile()
     else:
         tuned = head.autotune(args.path)   # GEMM tile width and transform kernel, timed on this batch
@@ -827,8 +823,6 @@ def gpu_arm(args, rank, world, local_rank):
                    "launch_settings": {"tile_width_setting": tuned["tn"],
                                        "transform": TRANSFORM_NAMES[tuned["fft"]],
                                        "transform_radix": head.plan(args.path).transform_radix,
-                                       "gemm_ksplit": head.plan(args.path).ksplit_info(B) if args.path == "split_fp16"
-                                       else None,
                                        "chosen_by": tuned["source"]},
                    "l2": "flushed (512 MiB write) before every timed step; the operator planes (%.0f MB) also "
                          "exceed L2" % (3 * (head.rows - 1) * head.Kp * 2 / 1e6),

@@ -439,8 +439,7 @@ LEG_API int leg_plan_autotune(leg_plan_t plan, const void *f, void *c, int B, cu
 
 /*
  * leg_forward_noalloc -- leg_forward for a LEG_SPLIT_FP16 plan that allocates
- * no device memory (its GEMM computes whole tiles: the results equal
- * leg_forward's with LEG_KSPLIT_OFF bit for bit).  (The paper has no counterpart: this is a library
+ * no device memory.  (The paper has no counterpart: this is a library
  * convenience.)  It is meant for callers that must not allocate at call time,
  * such as a host framework that owns the whole device-memory budget through
  * its own fixed pool, or a latency-critical caller that cannot afford the

@@ -427,19 +427,10 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         uint32_t cc = 0;
         int ti = 0;
         bool ok = true;
-        for (; ok; ++ti) {
-            // only the tile, the chunk count and the part's offset outlive the lookup
-            int tt, nch;
-            size_t part_off;
-            {
-                Seg sg;
-                if (!get_seg(ti, sg)) break;
-                tt = sg.t;
-                nch = (sg.kb1 - sg.kb0 + CHUNK_KB - 1) / CHUNK_KB;
-                part_off = ksplit ? (size_t)sg.part * (size_t)single.part_stride : 0;
-            }
+        Seg sg;
+        for (; ok && get_seg(ti, sg); ++ti) {
             int j0, b0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, tt, tn, j0, b0);
+            const TcProblem &pr = tile_problem(single, multi, nprob, sg.t, tn, j0, b0);
             // per-function scales of this warp's columns: lane l holds unit m's
             // column (l & 15); fetched before the accumulators are ready
             int fe[MU];
@@ -453,6 +444,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 16 * MU; ++i) r1[i] = 0.0f;
             if constexpr (NPROD > 1) {
+                const int nch = (sg.kb1 - sg.kb0 + CHUNK_KB - 1) / CHUNK_KB;
                 for (int ch = 0; ch < nch; ++ch, ++cc) {
                     const uint32_t b = cc % 2, u = cc / 2;
                     if (!warp_wait(&chunk_full[b], u & 1, wait_limit, &s_abort)) {
@@ -526,7 +518,8 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                         static_cast<float *>(pr.out)[o] = a0[16 * m + i];
                     } else if constexpr (OUT_DF) {
                         const dfl sm = df_two_sum(a0[16 * m + i], r1[16 * m + i] * pr.w1);
-                        static_cast<float2 *>(pr.out)[part_off + o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
+                        float2 *out = static_cast<float2 *>(pr.out) + (size_t)sg.part * pr.part_stride;
+                        out[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
                     } else {
                         static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], pr.w1, a0[16 * m + i]), e);
                     }

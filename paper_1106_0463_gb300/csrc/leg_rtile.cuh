@@ -427,51 +427,6 @@ __device__ __forceinline__ float2 gadd(float2 a, float2 b)   // double-float pai
     return make_float2(s.hi, s.lo);
 }
 
-// 16 bytes of G elements at dst (shared memory) += a (+ b): two FP64 or four
-// FP32 values, or two double-float pairs (hi, lo).
-template <class GT> __device__ __forceinline__ void chunk_add(unsigned char *dst, float4 a, float4 b, bool two);
-template <> __device__ __forceinline__ void chunk_add<double>(unsigned char *dst, float4 a, float4 b, bool two)
-{
-    double2 *d = reinterpret_cast<double2 *>(dst);
-    const double2 x = *reinterpret_cast<double2 *>(&a), y = *reinterpret_cast<double2 *>(&b);
-    double2 v = *d;
-    v.x += x.x;
-    v.y += x.y;
-    if (two) {
-        v.x += y.x;
-        v.y += y.y;
-    }
-    *d = v;
-}
-template <> __device__ __forceinline__ void chunk_add<float>(unsigned char *dst, float4 a, float4 b, bool two)
-{
-    float4 *d = reinterpret_cast<float4 *>(dst);
-    float4 v = *d;
-    v.x += a.x;
-    v.y += a.y;
-    v.z += a.z;
-    v.w += a.w;
-    if (two) {
-        v.x += b.x;
-        v.y += b.y;
-        v.z += b.z;
-        v.w += b.w;
-    }
-    *d = v;
-}
-template <> __device__ __forceinline__ void chunk_add<float2>(unsigned char *dst, float4 a, float4 b, bool two)
-{
-    float4 *d = reinterpret_cast<float4 *>(dst);
-    const float4 v = *d;
-    float2 lo = gadd(make_float2(v.x, v.y), make_float2(a.x, a.y));
-    float2 hi = gadd(make_float2(v.z, v.w), make_float2(a.z, a.w));
-    if (two) {
-        lo = gadd(lo, make_float2(b.x, b.y));
-        hi = gadd(hi, make_float2(b.z, b.w));
-    }
-    *d = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-
 template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
 __device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT *G, int ldg, int f, int t,
                                           const typename Ar<R>::GT *G2 = nullptr,
@@ -486,33 +441,21 @@ __device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT 
     const uint32_t dst = (uint32_t)__cvta_generic_to_shared(buf);
     for (int o = 16 * t; o < BYTES; o += 16 * D::T)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o), "l"(src + o) : "memory");
+    asm volatile("cp.async.wait_all;" ::: "memory");
     if (G2) {
-        // the parts' chunks of this thread, four sweeps' loads in flight at a
-        // time, added once the staged row has landed
-        constexpr int SWEEP = 16 * D::T;
-        const char *p2 = reinterpret_cast<const char *>(G2 + (size_t)f * ldg);
-        const char *p3 = G3 ? reinterpret_cast<const char *>(G3 + (size_t)f * ldg) : nullptr;
-        unsigned char *rowb = reinterpret_cast<unsigned char *>(buf);
-        for (int o0 = 16 * t; o0 < BYTES; o0 += 4 * SWEEP) {
-            float4 a[4], b[4];
+        constexpr int PER = 16 / (int)sizeof(GT);
+        GT *row = reinterpret_cast<GT *>(buf);
+        const size_t r0 = (size_t)f * ldg;
+        for (int o = 16 * t; o < BYTES; o += 16 * D::T) {
+            const int e0 = o / (int)sizeof(GT);
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int o = o0 + k * SWEEP;
-                a[k] = b[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (o < BYTES) {
-                    a[k] = __ldcg(reinterpret_cast<const float4 *>(p2 + o));
-                    if (p3) b[k] = __ldcg(reinterpret_cast<const float4 *>(p3 + o));
-                }
-            }
-            if (o0 == 16 * t) asm volatile("cp.async.wait_all;" ::: "memory");
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int o = o0 + k * SWEEP;
-                if (o < BYTES) chunk_add<GT>(rowb + o, a[k], b[k], p3 != nullptr);
+            for (int u = 0; u < PER; ++u) {
+                GT v = gadd(row[e0 + u], G2[r0 + e0 + u]);
+                if (G3) v = gadd(v, G3[r0 + e0 + u]);
+                row[e0 + u] = v;
             }
         }
     }
-    asm volatile("cp.async.wait_all;" ::: "memory");
     fsync<D::T>();
 }
 

@@ -4,9 +4,8 @@ budget through its own pool, or a latency-critical caller that cannot take
 cudaMalloc's host blocking).  Its intermediates live in the library's static
 64 MiB device array.
 
-Checked through the C ABI against leg_forward (whole GEMM tiles, as the
-entry point computes them) on two calls in a row: the same kernels on the same
-input, so the results must be identical bit for bit.
+Checked through the C ABI against leg_forward on two calls in a row: the same
+kernels on the same input, so the results must be identical bit for bit.
 Also: the largest batch that fits the array (its G region ends 3 KB before the
 array's end), the first batch that does not, and the plans it refuses.  This
 file is collected last on purpose.
@@ -54,7 +53,6 @@ def need_bytes(B, Kp, ldg):
 def test_noalloc_matches_leg_forward_twice(leg, N, M, K, B):
     lib, fn = _abi(leg)
     plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
-    plan.set_ksplit(leg.KSPLIT_OFF)   # the entry point computes whole tiles, as leg_forward then does
     rng = np.random.default_rng(K)
     stream = torch.cuda.current_stream()
     for call in range(2):   # two calls in a row, different inputs
@@ -79,7 +77,6 @@ def test_noalloc_largest_batch_that_fits(leg):
     lib, fn = _abi(leg)
     N, M, K = 512, 2048, 1025
     plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
-    plan.set_ksplit(leg.KSPLIT_OFF)   # the entry point computes whole tiles, as leg_forward then does
     Kp, ldg = 1056, 1056
     cap = 64 << 20
     B = 2888
