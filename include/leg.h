@@ -381,32 +381,6 @@ LEG_API int leg_plan_set_transform(leg_plan_t plan, int variant, int radix);
 LEG_API int leg_plan_get_transform(leg_plan_t plan, int *variant, int *radix);
 
 /*
- * leg_plan_set_ksplit -- how the forward tensor-core GEMM of a LEG_SPLIT_FP16
- * plan shares its work among the resident CTA pairs:
- *   LEG_KSPLIT_AUTO (default)  balanced K split when the library's cost model
- *                              expects it at least 5 % faster than whole
- *                              tiles (batches whose tiles leave pairs idle or
- *                              fill a second wave only in part);
- *   LEG_KSPLIT_OFF             whole tiles, round-robin over the pairs;
- *   LEG_KSPLIT_ON              balanced K split whenever it applies.
- * With the K split every pair takes an equal share of the (tile, K block)
- * work, so a tile may be computed in up to three parts by consecutive pairs;
- * each part is written to its own copy of G in the plan's workspace and the
- * transform adds the parts (a double-float sum) while it stages each row, so
- * no pair waits for another.  It applies to the register-tiled transforms
- * (not LEG_TRANSFORM_STOCKHAM), M >= 256, plans without LEG_FLAG_COLLAPSED,
- * and leg_forward / leg_forward_host (not leg_forward_noalloc or ragged
- * batches).  Results differ from whole tiles by the rounding of that sum.
- * leg_plan_ksplit_info -- for a batch of B: the mode, the tile width and the
- * parts per tile the forward GEMM uses (1 = whole tiles); any output may be NULL.
- */
-#define LEG_KSPLIT_AUTO 0
-#define LEG_KSPLIT_OFF  1
-#define LEG_KSPLIT_ON   2
-LEG_API int leg_plan_set_ksplit(leg_plan_t plan, int mode);
-LEG_API int leg_plan_ksplit_info(leg_plan_t plan, int B, int *mode, int *tn, int *parts);
-
-/*
  * leg_plan_tile_info -- the tile of the forward GEMM for a batch of B
  * functions: *tn functions per pair tile, *pairs CTA pairs resident at once
  * on the current device, *tiles pair tiles of the launch.  LEG_SPLIT_FP16
@@ -422,9 +396,7 @@ LEG_API int leg_plan_tile_info(leg_plan_t plan, int B, int *tn, int *pairs, int 
  * depend on it) and the forward transform (variant and radix, as
  * leg_plan_set_transform; the candidates compute the same map and differ by
  * rounding; plans created with LEG_FLAG_SINE_FORM keep the sine form and tune
- * its radix), and, for LEG_SPLIT_FP16 plans, the forward GEMM's work sharing
- * (leg_plan_set_ksplit; timed with the transform).  Not a step of the
- * paper's method: a tuning aid.
+ * its radix).  Not a step of the paper's method: a tuning aid.
  *   f  device, B x K input (as leg_forward);  c  device, B x N output buffer
  *      (overwritten).  Synchronises the stream; runs each candidate four times.
  *   *tn, *fft (either may be NULL): the chosen tile width (0 = the model's

@@ -22,7 +22,7 @@ import torch
 
 __all__ = [
     "F64", "F32", "BF16", "SPLIT_FP16", "FLAG_TAU_LITERAL", "FLAG_COLLAPSED", "FLAG_SINE_FORM",
-    "TRANSFORM_REG", "TRANSFORM_STOCKHAM", "TRANSFORM_SINE", "KSPLIT_AUTO", "KSPLIT_OFF", "KSPLIT_ON",
+    "TRANSFORM_REG", "TRANSFORM_STOCKHAM", "TRANSFORM_SINE",
     "FAMILY_GENFN", "FAMILY_EXP", "FAMILY_CHEB", "FAMILY_ABSPOW",
     "Ragged", "forward_ragged", "sample_cl",
     "LegError", "Plan", "LegendreFn", "legendre", "library_path", "declared_symbols", "load_library",
@@ -34,7 +34,6 @@ FLAG_TAU_LITERAL = 1
 FLAG_COLLAPSED = 2    # c = L f with L = R A multiplied out at plan time (one GEMM, no transform)
 FLAG_SINE_FORM = 4    # forward transform by the half-range sine form (Eq. 2.13)
 TRANSFORM_REG, TRANSFORM_STOCKHAM, TRANSFORM_SINE = 0, 1, 2
-KSPLIT_AUTO, KSPLIT_OFF, KSPLIT_ON = 0, 1, 2
 FAMILY_GENFN, FAMILY_EXP, FAMILY_CHEB, FAMILY_ABSPOW = 0, 1, 2, 3
 _ERR_NAMES = {1: "INVALID_ARG", 2: "OOM", 3: "CUDA", 4: "UNSUPPORTED", 5: "TIMEOUT"}
 
@@ -83,8 +82,6 @@ def _load():
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
         "leg_plan_set_transform": ([vp, i, i], i),
-        "leg_plan_set_ksplit": ([vp, i], i),
-        "leg_plan_ksplit_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_get_transform": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_tile_info": ([vp, i, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)], i),
@@ -254,17 +251,6 @@ class Plan:
         tn, fft = ctypes.c_int(), ctypes.c_int()
         _check(_lib.leg_plan_autotune(self._h, pf, pc, B, _stream(stream), ctypes.byref(tn), ctypes.byref(fft)))
         return {"tn": tn.value, "fft": fft.value}
-
-    def set_ksplit(self, mode: int):
-        """Work sharing of the forward split GEMM: KSPLIT_AUTO, KSPLIT_OFF or
-        KSPLIT_ON (leg_plan_set_ksplit)."""
-        _check(_lib.leg_plan_set_ksplit(self._h, int(mode)))
-
-    def ksplit_info(self, B: int) -> dict:
-        """Mode, tile width and parts per tile of the forward GEMM for B functions."""
-        m, tn, parts = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
-        _check(_lib.leg_plan_ksplit_info(self._h, int(B), ctypes.byref(m), ctypes.byref(tn), ctypes.byref(parts)))
-        return {"mode": m.value, "tn": tn.value, "parts": parts.value}
 
     def tile_info(self, B: int) -> dict:
         """Tile of the split forward GEMM for B functions: tn, resident pairs, tiles."""

@@ -18,7 +18,6 @@ void free_workspace(leg_plan *p)
 {
     leg_dev_free(p->G);
     leg_dev_free(p->Gbar);
-    p->Gparts = nullptr;
     leg_dev_free(p->Fh);
     p->Fh = nullptr;
     leg_dev_free(p->Fbf);
@@ -85,12 +84,8 @@ int alloc_workspace(leg_plan *p, int B)
         p->ldg = 0;   // one GEMM straight into c / df: no G
     } else {
         p->ldg = (p->dtype == LEG_SPLIT_FP16) ? bwdKp : rowsKp;
-        // split plans: G followed by the K-split GEMM's further partial outputs
-        const size_t gparts = (p->dtype == LEG_SPLIT_FP16) ? LEG_MAX_PARTS : 1;
-        LEG_CUDA_TRY(leg_dev_malloc(&p->G, eb * gparts * Bz * p->ldg));
+        LEG_CUDA_TRY(leg_dev_malloc(&p->G, eb * Bz * p->ldg));
         LEG_CUDA_TRY(leg_dev_malloc(&p->Gbar, eb * Bz * p->ldg));
-        if (gparts > 1) p->Gparts = static_cast<float2 *>(p->G) + Bz * p->ldg;
-        p->parts_cfg = -1;   // contents undefined: cleared before the first K-split launch
     }
     if (p->dtype == LEG_SPLIT_FP16) {
         // input planes serve both directions: B x Kp (forward) or B x bwdKp (adjoint)
@@ -411,11 +406,7 @@ int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, c
     }
     if (rc) return rc;
     if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[2], st));
-    // split plans: the K-split GEMM's partial outputs (parts_used, 1 = whole tiles)
-    if (p->dtype == LEG_SPLIT_FP16)
-        rc = leg_fft_forward_parts(p, p->G, p->ldg, p->parts_used, (long long)p->ws_B * p->ldg, c, B, st);
-    else
-        rc = leg_fft_forward(p, p->G, p->ldg, c, B, st);
+    rc = leg_fft_forward(p, p->G, p->ldg, c, B, st);
     if (rc) return rc;
     if (ev) LEG_CUDA_TRY(cudaEventRecord(ev[3], st));
     return LEG_OK;
@@ -445,7 +436,6 @@ extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStre
     key.tn = p->tn;
     key.fft = p->fft_variant;
     key.fft_log2e = p->fft_log2e;
-    key.ksplit = p->ksplit;
     key.wait = p->wait_limit;
     if (p->fwd_exec && key == p->fwd_key) {
         LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
@@ -615,29 +605,6 @@ extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
                                                       std::to_string(maxtn) + " for this plan");
     p->tn = tn;
     return LEG_OK;
-}
-
-extern "C" int leg_plan_set_ksplit(leg_plan_t p, int mode)
-{
-    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
-    if (mode < LEG_KSPLIT_AUTO || mode > LEG_KSPLIT_ON)
-        return leg_set_error(LEG_ERR_INVALID_ARG, "mode must be LEG_KSPLIT_AUTO, _OFF or _ON");
-    p->ksplit = mode;
-    return LEG_OK;
-}
-
-extern "C" int leg_plan_ksplit_info(leg_plan_t p, int B, int *mode, int *tn, int *parts)
-{
-    int rc = check_plan(p);
-    if (rc) return rc;
-    if (B < 1) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 1");
-    if (mode) *mode = p->ksplit;
-    if (p->dtype != LEG_SPLIT_FP16) {
-        if (tn) *tn = 0;
-        if (parts) *parts = 1;
-        return LEG_OK;
-    }
-    return leg_split_ksplit_info(p, B, tn, parts);
 }
 
 extern "C" int leg_plan_set_transform(leg_plan_t p, int variant, int radix)

@@ -108,7 +108,7 @@ template <class R, int LOG2H, int XE>
 __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE>()) dct16_forward_kernel(
     const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
     const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
-    const int *__restrict__ n_out, const typename Ar<R>::GT *__restrict__ G2, const typename Ar<R>::GT *__restrict__ G3)
+    const int *__restrict__ n_out)
 {
     using D = D16<LOG2H, XE>;
     using F = Fa<R>;
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
     using GT = typename Ar<R>::GT;
-    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t, G2, G3);
+    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t);
     const GT *g = reinterpret_cast<const GT *>(buf);
     // c_n for n < N reads X_0..X_N: X_2k for k <= N/2 and X_2k+1 for k <= (N-1)/2
     const int kmax = min(D::H - 1, N / 2);
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
 
 template <class R, int LOG2H, int XE>
 int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
-               const long long *out_off, const int *n_out, const void *G2, const void *G3)
+               const long long *out_off, const int *n_out)
 {
     using D = D16<LOG2H, XE>;
     auto kern = dct16_forward_kernel<R, LOG2H, XE>;
@@ -201,9 +201,7 @@ int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cu
     cfg.numAttrs = 1;
     LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, static_cast<const typename Ar<R>::GT *>(G), ldg,
                                     static_cast<typename Ar<R>::OUT *>(c), N, B,
-                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out,
-                                    static_cast<const typename Ar<R>::GT *>(G2),
-                                    static_cast<const typename Ar<R>::GT *>(G3)));
+                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out));
     return LEG_OK;
 }
 
@@ -223,7 +221,7 @@ int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw,
 
 template <class R, int LO, int HI>
 int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
-                 const int *rowfn, const long long *out_off, const int *n_out, const void *G2, const void *G3)
+                 const int *rowfn, const long long *out_off, const int *n_out)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
@@ -231,11 +229,11 @@ int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, 
         if (lg == LO) {
             // radix 16 differs from radix 8 only from H = 512 on (at least 32 threads of 16 values)
             if constexpr (LO >= 9) {
-                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
             }
-            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
         }
-        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }
 
@@ -255,12 +253,11 @@ int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const
 // H = 2^log2h with 6 <= log2h <= 13 (M = 4H from 256 to 32768); at most
 // 2^log2e values per thread (3: radix-8 passes, 4: radix-16).
 int leg_dct16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
-                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out,
-                      const void *G2, const void *G3)
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
 {
     if (dtype == LEG_F64)
-        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
-    return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
+    return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
 }
 
 int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,

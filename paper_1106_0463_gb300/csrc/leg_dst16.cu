@@ -77,7 +77,7 @@ template <class R, int LOG2H, int XE>
 __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE>()) dst16_forward_kernel(
     const typename Ar<R>::GT *__restrict__ G, int ldg, typename Ar<R>::OUT *__restrict__ c, int N, int B,
     const typename Ar<R>::TW *__restrict__ tw, const int *__restrict__ rowfn, const long long *__restrict__ out_off,
-    const int *__restrict__ n_out, const typename Ar<R>::GT *__restrict__ G2, const typename Ar<R>::GT *__restrict__ G3)
+    const int *__restrict__ n_out)
 {
     using D = D16<LOG2H, XE>;
     using F = Fa<R>;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE
     const bool live = blockIdx.x * D::FPB + grp < B;
     leg_griddep_wait();   // launched as a dependent of the GEMM that writes G
     using GT = typename Ar<R>::GT;
-    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t, G2, G3);
+    stage_row<R, LOG2H, XE>(buf, G, ldg, f, t);
     const GT *g = reinterpret_cast<const GT *>(buf);
     dst16<R, LOG2H, XE>(buf, t, tw, [&](int j) -> T_ { return GIn<R>::get(g, j); });
     if (!live) return;
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE
 
 template <class R, int LOG2H, int XE>
 int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
-               const long long *out_off, const int *n_out, const void *G2, const void *G3)
+               const long long *out_off, const int *n_out)
 {
     using D = D16<LOG2H, XE>;
     auto kern = dst16_forward_kernel<R, LOG2H, XE>;
@@ -133,15 +133,13 @@ int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cu
     cfg.numAttrs = 1;
     LEG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kern, static_cast<const typename Ar<R>::GT *>(G), ldg,
                                     static_cast<typename Ar<R>::OUT *>(c), N, B,
-                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out,
-                                    static_cast<const typename Ar<R>::GT *>(G2),
-                                    static_cast<const typename Ar<R>::GT *>(G3)));
+                                    static_cast<const typename Ar<R>::TW *>(tw), rowfn, out_off, n_out));
     return LEG_OK;
 }
 
 template <class R, int LO, int HI>
 int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st,
-                 const int *rowfn, const long long *out_off, const int *n_out, const void *G2, const void *G3)
+                 const int *rowfn, const long long *out_off, const int *n_out)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
@@ -149,11 +147,11 @@ int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, 
         if (lg == LO) {
             // radix 16 differs from radix 8 only from H = 512 on (at least 32 threads of 16 values)
             if constexpr (LO >= 9) {
-                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+                if (xe == 4) return launch_fwd<R, LO, 4>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
             }
-            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+            return launch_fwd<R, LO, 3>(G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
         }
-        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<R, LO + 1, HI>(lg, xe, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }
 
@@ -165,15 +163,14 @@ int dispatch_fwd(int lg, int xe, const void *G, int ldg, void *c, int N, int B, 
 // (float2), FP32 c, table of float4; LEG_F32 / LEG_BF16: FP32 G and c,
 // table of float2.
 int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
-                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out,
-                      const void *G2, const void *G3)
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out)
 {
     switch (dtype) {
     case LEG_F64:
-        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<double, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     case LEG_SPLIT_FP16:
-        return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<dfl, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     default:
-        return dispatch_fwd<float, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out, G2, G3);
+        return dispatch_fwd<float, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
 }

@@ -576,43 +576,27 @@ constexpr int DCT16_MIN_LOG2H = 6;
 
 int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, cudaStream_t st)
 {
-    return leg_fft_forward_parts(p, G, ldg, 1, 0, c, B, st);
-}
-
-int leg_fft_forward_parts(const leg_plan *p, const void *G, int ldg, int nparts, long long pstride, void *c, int B,
-                          cudaStream_t st)
-{
     if (B == 0) return LEG_OK;
     const int lg = ilog2(p->L);
-    const bool reg = lg - 1 >= DCT16_MIN_LOG2H && p->fft_variant != LEG_TRANSFORM_STOCKHAM;
-    if (nparts > 1 && (!reg || nparts > LEG_MAX_PARTS))
-        return leg_set_error(LEG_ERR_UNSUPPORTED, "partial outputs need a register-tiled transform");
-    // further parts of G, by element size
-    const size_t eb = p->dtype == LEG_F64 ? sizeof(double) : p->dtype == LEG_SPLIT_FP16 ? sizeof(float2)
-                                                                                         : sizeof(float);
-    const char *g0 = static_cast<const char *>(G);
-    const void *G2 = nparts > 1 ? g0 + (size_t)pstride * eb : nullptr;
-    const void *G3 = nparts > 2 ? g0 + 2 * (size_t)pstride * eb : nullptr;
     if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H) {
         const void *tw = p->dtype == LEG_F64 ? (const void *)p->tw64
                          : p->dtype == LEG_SPLIT_FP16 ? (const void *)p->twdf : (const void *)p->tw32;
         return leg_dst16_forward(p->dtype, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, tw, st, nullptr, nullptr,
-                                 nullptr, G2, G3);
+                                 nullptr);
     }
     switch (p->dtype) {
     case LEG_F64:
         if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_forward(LEG_F64, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->tw64, st, nullptr,
-                                     nullptr, nullptr, G2, G3);
+                                     nullptr, nullptr);
         return dispatch_dct_forward<double, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->tw64, st);
     case LEG_F32:
     case LEG_BF16:
-        if (nparts > 1) return leg_set_error(LEG_ERR_UNSUPPORTED, "partial outputs need a register-tiled transform");
         return dispatch_forward<float, 2, 14>(lg, G, ldg, c, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
         if (p->fft_variant == LEG_TRANSFORM_REG && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_forward(LEG_SPLIT_FP16, lg - 1, p->fft_log2e, G, ldg, c, p->N, B, p->twdf, st,
-                                     nullptr, nullptr, nullptr, G2, G3);
+                                     nullptr, nullptr, nullptr);
         return dispatch_dct_forward<dfl, 1, 13>(lg - 1, G, ldg, c, p->N, B, p->twdf, st);
     }
     return leg_set_error(LEG_ERR_INVALID_ARG, "bad dtype");

@@ -150,46 +150,6 @@ __device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, long l
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// The work of pair cid, as segments (tile t, K blocks [kb0, kb1), part q).
-// Without K split (nparts = 1 or a grouped launch): the whole tiles t = cid,
-// cid + ncl, ...  With K split (a single problem, nparts > 1): the pair's
-// equal share [cid W / ncl, (cid + 1) W / ncl) of the W = ntiles nkb
-// (tile, K block) pairs, cut at tile boundaries (at most MAX_SEGS segments,
-// which the host guarantees); the pairs that own parts of tile t are
-// consecutive, and the part index is the pair's rank among them.  Part q of a
-// tile with fewer than q + 1 parts is never written: the host clears the part
-// buffers whenever the segmentation changes, so those regions read as zero.
-constexpr int MAX_SEGS = 8;
-
-struct Seg {
-    int t, kb0, kb1;   // tile, K blocks
-    int part, nparts;  // this segment's part of tile t, parts of tile t
-};
-
-// The K-split segments of pair cid into segs[]; returns their number.
-__device__ int split_segments(int cid, int ncl, int ntiles, int nkb, Seg *segs)
-{
-    const long long W = (long long)ntiles * nkb;
-    // pair owning (tile, K block) pair g: the largest q with floor(q W / ncl) <= g
-    auto owner = [&](long long g) { return (int)(((g + 1) * ncl - 1) / W); };
-    long long g = (long long)cid * W / ncl;
-    const long long g1 = (long long)(cid + 1) * W / ncl;
-    int n = 0;
-    while (g < g1 && n < MAX_SEGS) {
-        Seg s;
-        s.t = (int)(g / nkb);
-        s.kb0 = (int)(g % nkb);
-        s.kb1 = (g1 - g < nkb - s.kb0) ? s.kb0 + (int)(g1 - g) : nkb;
-        const long long tg = (long long)s.t * nkb;
-        const int first = owner(tg);
-        s.part = cid - first;
-        s.nparts = owner(tg + nkb - 1) - first + 1;
-        segs[n++] = s;
-        g += s.kb1 - s.kb0;
-    }
-    return n;
-}
-
 // tn: functions per pair tile (multiple of 16, <= max_tn; every problem of the
 // launch uses it); stages: pipeline depth (<= MAX_STAGES, fits stage_bytes(tn)).
 template <int NPROD, bool OUT_DF>
@@ -214,8 +174,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     __shared__ __align__(8) uint64_t acc_empty;               // (even CTA) both epilogues have read them
     __shared__ __align__(8) uint64_t drain_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ Seg s_seg[MAX_SEGS];                           // K split: this pair's segments
-    __shared__ int s_nseg;
     __shared__ volatile int s_abort;
     __shared__ volatile uint32_t s_peer_issued;               // (even CTA) copies issued by the odd CTA
 
@@ -235,7 +193,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         sm100::mbar_init(&acc_full, 1);
         sm100::mbar_init(&acc_empty, 2 * EPI_WARPS);
         sm100::mbar_init(&drain_bar, 1);
-        s_nseg = (!multi && single.nparts > 1) ? split_segments(cid, ncl, ntiles, single.nkb, s_seg) : 0;
         s_abort = 0;
         s_peer_issued = 0;
         sm100::fence_mbar_init();
@@ -264,25 +221,6 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
     };
     const uint32_t bytes = NA * ATILE_BYTES + NF * FT;   // one CTA's copies per stage
     uint32_t issued = 0;                                  // producer: stages issued (lane 0 of warp 0)
-    const bool ksplit = !multi && single.nparts > 1;
-    // segment i of this pair (false past the last): a K-split segment from the
-    // table, or the whole tile cid + i ncl
-    auto get_seg = [&](int i, Seg &sg) -> bool {
-        if (ksplit) {
-            if (i >= s_nseg) return false;
-            sg = s_seg[i];
-            return true;
-        }
-        const int t = cid + i * ncl;
-        if (t >= ntiles) return false;
-        int j0_, b0_;
-        sg.t = t;
-        sg.kb0 = 0;
-        sg.kb1 = tile_problem(single, multi, nprob, t, tn, j0_, b0_).nkb;
-        sg.part = 0;
-        sg.nparts = 1;
-        return true;
-    };
 
     if (warp == 0) {
         // ------------------------------------------------ TMA producer warp (both CTAs)
@@ -293,12 +231,11 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         uint32_t s = 0, ph = 0;
         bool ok = true;
         const int half = tn >> 1;
-        Seg sg;
-        for (int si = 0; ok && get_seg(si, sg); ++si) {
+        for (int t = cid; ok && t < ntiles; t += ncl) {
             int j0, b0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, sg.t, tn, j0, b0);
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
             const int arow = j0 + (int)rank * CTA_M, frow = b0 + (int)rank * half;
-            for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+            for (int kb = 0; kb < pr.nkb; ++kb) {
                 if (!warp_wait(&empty_bar[s], ph ^ 1, wait_limit, &s_abort)) {
                     ok = false;
                     break;
@@ -334,8 +271,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         bool ok = true;
         const uint32_t idesc = sm100::idesc_f16(PAIR_M, tn, Cfg::BF16);
         int ti = 0;
-        Seg sg;
-        for (; ok && get_seg(ti, sg); ++ti) {
+        for (int t = cid; ok && t < ntiles; t += ncl, ++ti) {
+            int j0, b0;
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
             // acc0 / acc2 of the previous tile have been read by both epilogues
             if (!warp_wait(&acc_empty, (ti & 1) ^ 1, wait_limit, &s_abort)) {
                 ok = false;
@@ -344,7 +282,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
             sm100::tc_fence_after();
             const uint32_t acc2 = tmem + (uint32_t)tn;
             uint32_t acc1 = tmem + acc1_col(tn, 0);
-            for (int kb = sg.kb0; kb < sg.kb1; ++kb) {
+            for (int kb = 0; kb < pr.nkb; ++kb) {
                 if (!warp_wait(&full_bar[s], ph, wait_limit, &s_abort)) {
                     ok = false;
                     break;
@@ -355,7 +293,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                 const uint64_t d0 = sm100::desc_k_sw64(sm100::smem_u32(smem + s * SB));
                 auto A = [&](int p, int kk) { return d0 + (uint64_t)((p * ATILE_BYTES + kk * 32) >> 4); };
                 auto F = [&](int p, int kk) { return d0 + (uint64_t)((NA * ATILE_BYTES + p * FT + kk * 32) >> 4); };
-                const uint32_t first = (kb == sg.kb0) ? 0u : 1u;   // first K block of the segment
+                const uint32_t first = (kb == 0) ? 0u : 1u;   // first K block of the tile
                 if (leader) {
 #pragma unroll
                     for (int kk = 0; kk < TILE_K / 16; ++kk) {
@@ -373,7 +311,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                     }
                 }
                 if constexpr (NPROD > 1) {
-                    const int kc = (kb - sg.kb0) % CHUNK_KB;
+                    const int kc = kb % CHUNK_KB;
                     if (kc == 0) {   // a new acc1 chunk: its buffer must have been read
                         const uint32_t b = cc % nbuf, u = cc / nbuf;
                         if (!warp_wait(&chunk_empty[b], (u & 1) ^ 1, wait_limit, &s_abort)) {
@@ -391,9 +329,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                             sm100::mma_f16_pair(acc1, A(0, kk), F(1, kk), idesc, 1u);   // A0 F1
                         }
                         sm100::mma_commit_pair_mc(&empty_bar[s], 0x3);
-                        if (kc == CHUNK_KB - 1 || kb == sg.kb1 - 1) sm100::mma_commit_pair_mc(&chunk_full[cc % nbuf], 0x3);
+                        if (kc == CHUNK_KB - 1 || kb == pr.nkb - 1) sm100::mma_commit_pair_mc(&chunk_full[cc % nbuf], 0x3);
                     }
-                    if (kc == CHUNK_KB - 1 || kb == sg.kb1 - 1) ++cc;
+                    if (kc == CHUNK_KB - 1 || kb == pr.nkb - 1) ++cc;
                 } else {
                     if (leader) sm100::mma_commit_pair_mc(&empty_bar[s], 0x3);
                 }
@@ -427,10 +365,9 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
         uint32_t cc = 0;
         int ti = 0;
         bool ok = true;
-        Seg sg;
-        for (; ok && get_seg(ti, sg); ++ti) {
+        for (int t = cid; ok && t < ntiles; t += ncl, ++ti) {
             int j0, b0;
-            const TcProblem &pr = tile_problem(single, multi, nprob, sg.t, tn, j0, b0);
+            const TcProblem &pr = tile_problem(single, multi, nprob, t, tn, j0, b0);
             // per-function scales of this warp's columns: lane l holds unit m's
             // column (l & 15); fetched before the accumulators are ready
             int fe[MU];
@@ -444,7 +381,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
 #pragma unroll
             for (int i = 0; i < 16 * MU; ++i) r1[i] = 0.0f;
             if constexpr (NPROD > 1) {
-                const int nch = (sg.kb1 - sg.kb0 + CHUNK_KB - 1) / CHUNK_KB;
+                const int nch = (pr.nkb + CHUNK_KB - 1) / CHUNK_KB;
                 for (int ch = 0; ch < nch; ++ch, ++cc) {
                     const uint32_t b = cc % 2, u = cc / 2;
                     if (!warp_wait(&chunk_full[b], u & 1, wait_limit, &s_abort)) {
@@ -518,8 +455,7 @@ __global__ void __launch_bounds__(THREADS, 1) tc_gemm_kernel(const __grid_consta
                         static_cast<float *>(pr.out)[o] = a0[16 * m + i];
                     } else if constexpr (OUT_DF) {
                         const dfl sm = df_two_sum(a0[16 * m + i], r1[16 * m + i] * pr.w1);
-                        float2 *out = static_cast<float2 *>(pr.out) + (size_t)sg.part * pr.part_stride;
-                        out[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
+                        static_cast<float2 *>(pr.out)[o] = make_float2(scale2(sm.hi, e), scale2(sm.lo, e));
                     } else {
                         static_cast<float *>(pr.out)[o] = scale2(fmaf(r1[16 * m + i], pr.w1, a0[16 * m + i]), e);
                     }
@@ -858,7 +794,7 @@ int max_pairs(int *out)
 
 template <int NPROD, bool OUT_DF>
 int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int ntiles, int tn, int *status,
-              long long limit, cudaStream_t st, bool all_pairs = false)
+              long long limit, cudaStream_t st)
 {
     if (ntiles <= 0) return LEG_OK;
     if (tn < 16 || tn > max_tn<NPROD>() || tn % 16)
@@ -870,7 +806,7 @@ int launch_tc(const TcProblem &single, const TcProblem *multi, int nprob, int nt
     int pairs = 0;
     int rc = max_pairs(&pairs);
     if (rc) return rc;
-    const int npairs = (ntiles < pairs && !all_pairs) ? ntiles : pairs;   // K split: every pair takes a share
+    const int npairs = ntiles < pairs ? ntiles : pairs;
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute at[2];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -944,8 +880,6 @@ void finish_problem(TcProblem *pr, const int *aexp, const int *fexp, void *out, 
     pr->ntn = ceil_div(B, tn);
     pr->tile0 = 0;
     pr->w1 = 1.0f;
-    pr->nparts = 1;
-    pr->part_stride = 0;
 }
 
 // Split problem: operator planes a0 + s apstride (rows x Kc, row stride lda),
@@ -1034,81 +968,9 @@ int leg_gemm_split_fwd_into(leg_plan *p, int B, const LegSplitIn &in, float2 *G,
     return launch_tc<8, true>(pr, nullptr, 1, tiles_of(pr), pr.tn, p->status, p->wait_limit, st);
 }
 
-// The balanced K split of the forward GEMM for B functions (the segments of
-// tc_gemm_kernel): whether to use it, its tile width and the most parts a
-// tile is cut into.  Used when the plan allows it (LEG_KSPLIT_AUTO: when the
-// cost model expects it 5 % faster than whole tiles, e.g. a batch whose tiles
-// leave resident pairs idle or fill a second wave partly; LEG_KSPLIT_ON:
-// whenever it is possible), the transform is register-tiled (it sums the
-// parts), no tile is cut into more than LEG_MAX_PARTS parts and no pair gets
-// more than MAX_SEGS segments.
-bool ksplit_decide(const leg_plan *p, int B, int *tn_out, int *nparts_out, int *ntiles_out, int *pairs_out)
-{
-    if (p->ksplit == LEG_KSPLIT_OFF || p->collapsed() || p->fft_variant == LEG_TRANSFORM_STOCKHAM || p->M < 256)
-        return false;
-    int pairs = 0;
-    if (max_pairs(&pairs)) return false;
-    const int ntm = ceil_div(leg_split_fwd_rows(p), PAIR_M), nkb = p->Kp / TILE_K;
-    const int tn = p->tn ? p->tn : max_tn<8>();
-    const long long ntiles = (long long)ntm * ceil_div(B, tn);
-    const long long W = ntiles * nkb;
-    if (W < 2LL * pairs || ntiles > (1 << 24)) return false;
-    const long long share = (W + pairs - 1) / pairs;
-    const long long segs = (share + nkb - 1) / nkb + 1;
-    if (segs > MAX_SEGS) return false;
-    int nparts = 1;
-    auto owner = [&](long long g) { return (long long)(((g + 1) * pairs - 1) / W); };
-    for (long long t = 0; t < ntiles; ++t) {
-        const long long n = owner(t * nkb + nkb - 1) - owner(t * nkb) + 1;
-        if (n > nparts) nparts = (int)n;
-    }
-    if (nparts > LEG_MAX_PARTS) return false;
-    if (p->ksplit == LEG_KSPLIT_AUTO) {
-        const long long whole = tile_cost(leg_split_choose_tn(p, B), ntm, B, nkb, pairs);
-        const long long split = share * 16 * mma_cycles(tn) + 2000 * segs;
-        if (!(split < 0.95 * (double)whole)) return false;
-    }
-    *tn_out = tn;
-    *nparts_out = nparts;
-    *ntiles_out = (int)ntiles;
-    *pairs_out = pairs;
-    return true;
-}
-
 int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st)
 {
-    const LegSplitIn in = leg_split_workspace(p);
-    int tn = 0, nparts = 1, ntiles = 0, pairs = 0;
-    if (!p->Gparts || !ksplit_decide(p, B, &tn, &nparts, &ntiles, &pairs)) {
-        p->parts_used = 1;
-        return leg_gemm_split_fwd_into(p, B, in, static_cast<float2 *>(p->G), p->ldg, st);
-    }
-    TcProblem pr;
-    int rc = leg_make_split_problem(&pr, p, in, B, static_cast<float2 *>(p->G), p->ldg, tn);
-    if (rc) return rc;
-    pr.nparts = nparts;
-    pr.part_stride = (long long)p->ws_B * p->ldg;
-    // parts a tile lacks must read as zero: clear them when the segmentation
-    // (and so which regions are written) changes
-    const long long cfg = (((long long)B * 131 + tn) * 7 + nparts) * 4099 + pairs;
-    if (cfg != p->parts_cfg) {
-        LEG_CUDA_TRY(cudaMemsetAsync(p->Gparts, 0, sizeof(float2) * (LEG_MAX_PARTS - 1) * (size_t)p->ws_B * p->ldg, st));
-        p->parts_cfg = cfg;
-    }
-    p->parts_used = nparts;
-    return launch_tc<8, true>(pr, nullptr, 1, ntiles, tn, p->status, p->wait_limit, st, true);
-}
-
-int leg_split_ksplit_info(const leg_plan *p, int B, int *tn, int *nparts)
-{
-    int t = 0, n = 1, nt = 0, np = 0;
-    if (!ksplit_decide(p, B, &t, &n, &nt, &np)) {
-        t = leg_split_choose_tn(p, B);
-        n = 1;
-    }
-    if (tn) *tn = t;
-    if (nparts) *nparts = n;
-    return LEG_OK;
+    return leg_gemm_split_fwd_into(p, B, leg_split_workspace(p), static_cast<float2 *>(p->G), p->ldg, st);
 }
 
 // df[b, k] = sum_j in[b, j] S[j, k] from the split planes `in` (B x npr) of

@@ -158,8 +158,7 @@ extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, 
             if ((rc = leg_gemm_split_fwd(p, B, st))) return rc;
             for (int i = 0; i < nch; ++i) {
                 const int b0 = off(i), nb = off(i + 1) - b0;
-                rc = leg_fft_forward_parts(p, G + (size_t)b0 * p->ldg, p->ldg, p->parts_used,
-                                           (long long)p->ws_B * p->ldg, cd + crow * b0, nb, st);
+                rc = leg_fft_forward(p, G + (size_t)b0 * p->ldg, p->ldg, cd + crow * b0, nb, st);
                 if (rc) return rc;
                 LEG_CUDA_TRY(cudaEventRecord(h->out[i], st));
                 LEG_CUDA_TRY(cudaStreamWaitEvent(h->d2h, h->out[i], 0));

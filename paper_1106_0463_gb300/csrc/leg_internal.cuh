@@ -75,7 +75,6 @@ __host__ __device__ inline int leg_split_fbits(int K) { return K <= 1025 ? 8 : 7
 // (leg_gemm_tc.cu).
 constexpr int LEG_SPLIT_NA = 3;
 constexpr int LEG_SPLIT_NF = 7;
-constexpr int LEG_MAX_PARTS = 3;   // partial outputs per tile of the K-split GEMM, at most
 
 // ---------------------------------------------------------------------------
 // Plan.
@@ -110,13 +109,6 @@ struct leg_plan {
     int *rowexp = nullptr;                        // per-row power-of-two scale (split)
     double a00 = 0.0;         // A[0,0] = sum_q w_q: row 0 (y = 0, x = 1) is a00 times f at x = 1
     int tn = 0;               // functions per tensor-core pair tile (0: chosen per launch)
-    int ksplit = 0;           // LEG_KSPLIT_*: balanced K split of the forward split GEMM
-    // the split GEMM's partial outputs (parts 1..LEG_MAX_PARTS-1 of G, right
-    // after G in its allocation) and the segmentation they were last written
-    // under (a change clears them, so that parts a tile lacks read as zero)
-    float2 *Gparts = nullptr;
-    long long parts_cfg = -1;
-    int parts_used = 1;       // parts of the last forward GEMM (1: whole tiles)
     int fft_variant = 0;      // LEG_TRANSFORM_*: the forward transform kernel (same map, rounding differs)
     int fft_log2e = 3;        // register-tiled forward transforms: 2^fft_log2e values per thread (radix 8 or 16)
     bool collapsed() const { return (flags & LEG_FLAG_COLLAPSED) != 0; }
@@ -152,12 +144,12 @@ struct leg_plan {
         void *c = nullptr;
         int B = 0, wsB = 0;   // wsB: the workspace's capacity (plane strides depend on it)
         void *G = nullptr, *Fh = nullptr;
-        int tn = 0, fft = 0, fft_log2e = 0, ksplit = 0;
+        int tn = 0, fft = 0, fft_log2e = 0;
         long long wait = 0;
         bool operator==(const GraphKey &o) const
         {
             return f == o.f && c == o.c && B == o.B && wsB == o.wsB && G == o.G && Fh == o.Fh && tn == o.tn &&
-                   fft == o.fft && fft_log2e == o.fft_log2e && ksplit == o.ksplit && wait == o.wait;
+                   fft == o.fft && fft_log2e == o.fft_log2e && wait == o.wait;
         }
     };
     GraphKey fwd_key;
@@ -222,13 +214,6 @@ struct TcProblem {
     int ntm, ntn;            // tiles along rows (256 each) and along functions (tn each)
     int tile0;               // first global tile index of this problem (grouped launches)
     float w1;                // 2^-s: weight of acc1 and acc2 (split path)
-    // balanced K split (single split problems with a double-float output):
-    // the (tile, K block) work is shared equally by all resident pairs; a
-    // tile cut between pairs leaves one partial output per pair, part q at
-    // out + q * part_stride, parts up to nparts - 1 (zero where a tile has
-    // fewer parts); nparts = 1: whole tiles, the output is G itself
-    int nparts;
-    long long part_stride;   // elements between parts (float2)
 };
 
 // Device descriptor of one bucket of a ragged batch (input-split targets).
@@ -266,10 +251,6 @@ int leg_gemm_f32_adj(const float *Gb, int ldg, const float *A, int lda, float *D
 //   adjoint: gbar[b, j] = (w_j / M) sum_{n<=N} d_n cos(2 pi n j / M), d_n = (2n+1)v_n - (2n-1)v_{n-1}
 // gkind: 0 = double G, 1 = float G, 2 = double-float G (float2)
 int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, cudaStream_t st);
-// the same, G the sum of nparts partial outputs G + q pstride (q < nparts <= 3;
-// register-tiled transforms only, which sum them while staging each row)
-int leg_fft_forward_parts(const leg_plan *p, const void *G, int ldg, int nparts, long long pstride, void *c, int B,
-                          cudaStream_t st);
 int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B, cudaStream_t st);
 int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, int B, cudaStream_t st);
 
@@ -288,17 +269,14 @@ constexpr int LEG_TRANSFORM_MIN_M_REG = 256;   // smallest M of the register-til
 // register-tiled transforms (leg_dct16.cu), H = 2^log2h with 6 <= log2h <= 13;
 // dtype LEG_F64 (FP64 G, c) or LEG_SPLIT_FP16 (double-float G, FP32 c)
 // log2e: at most 2^log2e values per thread (3 or 4: radix-8 or radix-16 passes)
-// G2, G3: further partial outputs to add to G (or null)
 int leg_dct16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
-                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out,
-                      const void *G2 = nullptr, const void *G3 = nullptr);
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
                       cudaStream_t st);
 // register-tiled sine form (leg_dst16.cu), same H range; dtype LEG_F64,
 // LEG_SPLIT_FP16 (double-float G, FP32 c) or LEG_F32 / LEG_BF16 (FP32)
 int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
-                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out,
-                      const void *G2 = nullptr, const void *G3 = nullptr);
+                      const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,
@@ -334,8 +312,6 @@ int leg_split_prepare_input_into(const leg_plan *p, const float *f, int B, const
 int leg_gemm_split_fwd_into(leg_plan *p, int B, const LegSplitIn &in, float2 *G, int ldg, cudaStream_t st);
 // functions per pair tile for a forward of B functions (plan override, else the wave-count rule)
 int leg_split_choose_tn(const leg_plan *p, int B);
-// the forward GEMM's tile width and parts per tile for B functions (parts 1: whole tiles)
-int leg_split_ksplit_info(const leg_plan *p, int B, int *tn, int *nparts);
 // resident CTA pairs of the tensor-core GEMM on the current device; estimated
 // cycles of the busiest pair for ntm row tiles x B functions of K-depth nkb
 int leg_split_max_pairs(int *pairs);

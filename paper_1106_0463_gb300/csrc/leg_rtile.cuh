@@ -417,20 +417,8 @@ __device__ __forceinline__ void fft16(CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> *bu
 // aligned with at least one padding element) in buf, which the transform's
 // first step reads before the first FFT pass overwrites it: every 16-byte
 // copy of the row is in flight at once.  Synchronises the function's threads.
-// G2, G3 (or null): further partial outputs of a K-split GEMM, added to the
-// staged row by the thread that staged each 16-byte chunk.
-__device__ __forceinline__ double gadd(double a, double b) { return a + b; }
-__device__ __forceinline__ float gadd(float a, float b) { return a + b; }
-__device__ __forceinline__ float2 gadd(float2 a, float2 b)   // double-float pairs (hi, lo)
-{
-    const dfl s = df_add(dfl{a.x, a.y}, dfl{b.x, b.y});
-    return make_float2(s.hi, s.lo);
-}
-
 template <class R, int LOG2H, int XE = LEG_DCT16_LOG2E>
-__device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT *G, int ldg, int f, int t,
-                                          const typename Ar<R>::GT *G2 = nullptr,
-                                          const typename Ar<R>::GT *G3 = nullptr)
+__device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT *G, int ldg, int f, int t)
 {
     using D = D16<LOG2H, XE>;
     using GT = typename Ar<R>::GT;
@@ -442,20 +430,6 @@ __device__ __forceinline__ void stage_row(CxT<R> *buf, const typename Ar<R>::GT 
     for (int o = 16 * t; o < BYTES; o += 16 * D::T)
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + o), "l"(src + o) : "memory");
     asm volatile("cp.async.wait_all;" ::: "memory");
-    if (G2) {
-        constexpr int PER = 16 / (int)sizeof(GT);
-        GT *row = reinterpret_cast<GT *>(buf);
-        const size_t r0 = (size_t)f * ldg;
-        for (int o = 16 * t; o < BYTES; o += 16 * D::T) {
-            const int e0 = o / (int)sizeof(GT);
-#pragma unroll
-            for (int u = 0; u < PER; ++u) {
-                GT v = gadd(row[e0 + u], G2[r0 + e0 + u]);
-                if (G3) v = gadd(v, G3[r0 + e0 + u]);
-                row[e0 + u] = v;
-            }
-        }
-    }
     fsync<D::T>();
 }
 

@@ -8,9 +8,7 @@
 //     transform, the shared-memory Stockham one, or the register-tiled sine
 //     form (Eq. 2.13), the register-tiled ones with radix-8 or radix-16
 //     passes (8 or 16 values per thread, for H = M/4 >= 512); plans created
-//     with LEG_FLAG_SINE_FORM keep the sine form and tune its radix;
-//   * the work sharing of the forward split GEMM: whole tiles or the balanced
-//     K split (leg_plan_set_ksplit), timed together with the transform.
+//     with LEG_FLAG_SINE_FORM keep the sine form and tune its radix.
 //
 // Each candidate runs once untimed and three times timed (CUDA events around
 // the stage, on the caller's stream); the fastest median wins and is stored
@@ -78,7 +76,7 @@ std::string tune_key(const leg_plan *p, int B)
     return buf;
 }
 
-// Median of `reps` timings of stage `stage` (0 split, 1 GEMM, 2 FFT, 3 GEMM + FFT) of the forward pass.
+// Median of `reps` timings of stage `stage` (0 split, 1 GEMM, 2 FFT) of the forward pass.
 int time_stage(leg_plan *p, const void *f, void *c, int B, cudaStream_t st, int stage, int reps, float *out)
 {
     float ms[3];
@@ -87,7 +85,7 @@ int time_stage(leg_plan *p, const void *f, void *c, int B, cudaStream_t st, int 
     std::vector<float> v;
     for (int r = 0; r < reps; ++r) {
         if ((rc = leg_forward_profiled(p, f, c, B, st, ms))) return rc;
-        v.push_back(stage == 3 ? ms[1] + ms[2] : ms[stage]);
+        v.push_back(ms[stage]);
     }
     std::sort(v.begin(), v.end());
     *out = v[v.size() / 2];
@@ -105,23 +103,20 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
     std::lock_guard<std::mutex> lock(leg_tune_mutex());
     const char *path = getenv("LEG_TUNE_CACHE");
     const std::string key = tune_key(p, B);
-    // cache fields: tile width + K-split mode code, transform variant + radix code
-    int tn = p->tn | (p->ksplit << 16), fft = p->fft_variant | (p->fft_log2e << 4);
+    int tn = p->tn, fft = p->fft_variant | (p->fft_log2e << 4);   // cache field: variant + radix code
     const bool tc = (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16);
     const int maxtn = (p->dtype == LEG_BF16) ? 256 : 128;
     const bool sine_fixed = (p->flags & LEG_FLAG_SINE_FORM) != 0;
-    auto valid = [&](int wcode, int code) {
-        const int v = code & 15, e = code >> 4, w = wcode & 0xffff, ks = wcode >> 16;
-        const bool tn_ok = (w == 0 || (tc && w >= 16 && w <= maxtn && w % 16 == 0)) && ks >= LEG_KSPLIT_AUTO &&
-                           ks <= LEG_KSPLIT_ON;
+    auto valid = [&](int w, int code) {
+        const int v = code & 15, e = code >> 4;
+        const bool tn_ok = w == 0 || (tc && w >= 16 && w <= maxtn && w % 16 == 0);
         const bool fft_ok = v >= LEG_TRANSFORM_REG && v <= LEG_TRANSFORM_SINE && (e == 3 || e == 4) &&
                             (v != LEG_TRANSFORM_SINE || p->M >= LEG_TRANSFORM_MIN_M_REG) &&
                             (!sine_fixed || v == LEG_TRANSFORM_SINE);
         return tn_ok && fft_ok;
     };
     if (path && *path && leg_tune_cache_lookup(path, key, &tn, &fft) && valid(tn, fft)) {
-        p->tn = tn & 0xffff;
-        p->ksplit = tn >> 16;
+        p->tn = tn;
         p->fft_variant = fft & 15;
         p->fft_log2e = fft >> 4;
     } else {
@@ -183,28 +178,7 @@ extern "C" int leg_plan_autotune(leg_plan_t p, const void *f, void *c, int B, cu
             p->fft_variant = best_c.first;
             p->fft_log2e = best_c.second;
         }
-        if (p->dtype == LEG_SPLIT_FP16 && !p->collapsed()) {
-            // the forward GEMM's work sharing: the model's choice, whole tiles,
-            // or the balanced K split (timed with the transform, which adds the parts)
-            const int modes[3] = {LEG_KSPLIT_AUTO, LEG_KSPLIT_OFF, LEG_KSPLIT_ON};
-            float best = -1.0f;
-            int best_m = LEG_KSPLIT_AUTO;
-            for (int m : modes) {
-                p->ksplit = m;
-                float t;
-                if ((rc = time_stage(p, f, c, B, st, 3, 3, &t))) {
-                    p->ksplit = LEG_KSPLIT_AUTO;
-                    return rc;
-                }
-                if (best < 0 || t < best * 0.99f) {
-                    best = t;
-                    best_m = m;
-                }
-            }
-            p->ksplit = best_m;
-        }
-        if (path && *path)
-            leg_tune_cache_store(path, key, p->tn | (p->ksplit << 16), p->fft_variant | (p->fft_log2e << 4));
+        if (path && *path) leg_tune_cache_store(path, key, p->tn, p->fft_variant | (p->fft_log2e << 4));
     }
     if (tn_out) *tn_out = p->tn;
     if (fft_out) *fft_out = p->fft_variant;   // the radix: leg_plan_get_transform
