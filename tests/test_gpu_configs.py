@@ -70,7 +70,8 @@ def test_bench_workload_all_paths(leg, oracle):
     print("bench workload errors", errs)
     assert errs["split"] < 1e-6
     assert errs["f64"] < 1e-11
-    assert errs["f32"] < 3e-4
+    # measured 5.6e-5 (FP32 GEMM + FP32 transform); the bound leaves 2.5x
+    assert errs["f32"] < 1.5e-4
 
 
 def test_precision_sweep(leg, oracle):
@@ -89,8 +90,10 @@ def test_precision_sweep(leg, oracle):
     print("precision sweep errors", errs)
     assert errs["f64"] < 1e-11
     assert errs["split_fp16"] < 1e-6
-    assert errs["f32"] < 2e-3
-    assert errs["bf16"] < 0.2
+    # measured 2.4e-4 (FP32) and 8.3e-3 (one BF16 product) on these 40
+    # functions; the bounds leave 2.5x, so a drop in either path's accuracy shows
+    assert errs["f32"] < 6e-4
+    assert errs["bf16"] < 2.1e-2
 
 
 def test_differentiation(leg, oracle):
