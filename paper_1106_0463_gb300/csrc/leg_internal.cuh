@@ -117,7 +117,8 @@ struct leg_plan {
     __half *AhT[3] = {nullptr, nullptr, nullptr};   // one allocation (AhT[s] = AhT[0] + s K Kpr)
     int *colexp = nullptr;
 
-    // twiddles e^{2 pi i n / M}, n = 0..M-1 (computed in FP64 on the device)
+    // twiddles e^{2 pi i n / M}, n = 0..M-1 (computed in FP64 on the device),
+    // followed by the compact copy e^{2 pi i q / (M/4)}, q < M/4 (entries M..)
     double2 *tw64 = nullptr;
     float2 *tw32 = nullptr;
     float4 *twdf = nullptr;   // (re.hi, re.lo, im.hi, im.lo)

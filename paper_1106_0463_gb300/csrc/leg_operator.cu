@@ -238,12 +238,16 @@ void transpose_f64(const double *in, int ldi, double *out, int ldo, int R, int C
     transpose_f64_kernel<<<grid, block>>>(in, ldi, out, ldo, R, C);
 }
 
+// e^{2 pi i n / M} for n < M, then (entries M .. M + M/4 - 1) the compact copy
+// e^{2 pi i q / (M/4)} = entry 4q, which the register-tiled FFT passes read
+// (their twiddle indices are multiples of 4: a table a quarter the size).
 __global__ void twiddle_kernel(int M, double2 *t64, float2 *t32, float4 *tdf)
 {
     int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= M) return;
+    if (n >= M + M / 4) return;
+    const int m = n < M ? n : 4 * (n - M);
     double s, c;
-    sincospi(2.0 * n / M, &s, &c);
+    sincospi(2.0 * m / M, &s, &c);
     t64[n] = make_double2(c, s);
     t32[n] = make_float2((float)c, (float)s);
     float ch = (float)c, sh = (float)s;
@@ -254,10 +258,11 @@ __global__ void twiddle_kernel(int M, double2 *t64, float2 *t32, float4 *tdf)
 
 int leg_build_twiddles(leg_plan *p)
 {
-    LEG_CUDA_TRY(leg_dev_malloc(&p->tw64, sizeof(double2) * p->M));
-    LEG_CUDA_TRY(leg_dev_malloc(&p->tw32, sizeof(float2) * p->M));
-    LEG_CUDA_TRY(leg_dev_malloc(&p->twdf, sizeof(float4) * p->M));
-    twiddle_kernel<<<(p->M + 255) / 256, 256>>>(p->M, p->tw64, p->tw32, p->twdf);
+    const size_t n = (size_t)p->M + p->M / 4;   // the full table and its compact copy
+    LEG_CUDA_TRY(leg_dev_malloc(&p->tw64, sizeof(double2) * n));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->tw32, sizeof(float2) * n));
+    LEG_CUDA_TRY(leg_dev_malloc(&p->twdf, sizeof(float4) * n));
+    twiddle_kernel<<<(int)((n + 255) / 256), 256>>>(p->M, p->tw64, p->tw32, p->twdf);
     LEG_LAUNCH_CHECK("twiddle_kernel");
     return LEG_OK;
 }

@@ -6,7 +6,7 @@
 // H = 512).  The FFT is a Stockham autosort of radix-E
 // passes (the last pass takes the remaining power of two): each thread holds
 // x[t + b T], b < E, forms E/R radix-R butterflies from them, applies the
-// inter-pass twiddles (M-th roots of unity from the FP64-built table),
+// inter-pass twiddles (H-th roots of unity from the compact FP64-built table),
 // transforms in registers (a radix-2 network with constant twiddles) and
 // writes the outputs to their autosorted positions in shared memory, padded by
 // one slot per E values to avoid bank conflicts.  Double-float sums and
@@ -284,7 +284,10 @@ __device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> 
     using D = D16<LOG2H, XE>;
     using F = Fa<R>;
     constexpr int E = D::E, T = D::T, NB = E / P;
-    const int tstep = D::M / (P * Ns);
+    // e^{2 pi i r k / (P Ns)} = entry r k H / (P Ns) of the compact table of
+    // H = M/4 entries that follows the full one (a quarter of the cache footprint)
+    const int tstep = D::H / (P * Ns);
+    const typename Ar<R>::TW *twc = tw + D::M;
 #pragma unroll
     for (int bb = 0; bb < NB; ++bb) {
         const int j = t + bb * T;
@@ -296,7 +299,7 @@ __device__ __forceinline__ void fft_pass(CxT<R> (&v)[D16<LOG2H, XE>::E], CxT<R> 
 #pragma unroll
             for (int r = 1; r < P; ++r) {
                 typename F::T c, s;
-                twid(tw, r * k * tstep, c, s);
+                twid(twc, r * k * tstep, c, s);
                 x[r] = cmul<R>(x[r], c, s);
             }
         }
