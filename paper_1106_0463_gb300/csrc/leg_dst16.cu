@@ -42,20 +42,26 @@ __device__ __forceinline__ void dst16(CxT<R> *buf, int t, const typename Ar<R>::
     using T_ = typename F::T;
     constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
     CxT<R> v[E];
-    // W_k of the merged pre-twiddle (k = 0..H)
-    auto wk = [&](int k) -> CxT<R> {
-        if (k == 0) return {F::pow2(load(L), 1), F::zero()};
-        const T_ a = load(k), b = load(L - k);
+    // W_k and W_{H-k} of the merged pre-twiddle (k < H) from one table entry:
+    // e^{2 pi i (H - k) / M} = i e^{-2 pi i k / M} = (s, c) for (c, s) = e^{2 pi i k / M}
+    auto wpair = [&](int k, CxT<R> &w, CxT<R> &u) {
         T_ c, s;
-        twid(tw, k, c, s);   // e^{2 pi i k / M}
-        const T_ d = F::sub(b, a);
-        return {F::add(F::add(a, b), F::mul(c, d)), F::mul(s, d)};
+        twid(tw, k, c, s);
+        if (k == 0) {
+            w = {F::pow2(load(L), 1), F::zero()};
+        } else {
+            const T_ a = load(k), b = load(L - k), d = F::sub(b, a);
+            w = {F::add(F::add(a, b), F::mul(c, d)), F::mul(s, d)};
+        }
+        const T_ a = load(H - k), b = load(H + k), d = F::sub(b, a);
+        u = {F::add(F::add(a, b), F::mul(s, d)), F::mul(c, d)};
     };
     // 1. Y_k for k = t + b T
 #pragma unroll
     for (int b = 0; b < E; ++b) {
         const int k = t + b * T;
-        const CxT<R> w = wk(k), u = wk(H - k);
+        CxT<R> w, u;
+        wpair(k, w, u);
         // W_k + conj W_{H-k} and W_k - conj W_{H-k}
         const T_ pre = F::add(w.re, u.re), pim = F::sub(w.im, u.im);
         const T_ dre = F::sub(w.re, u.re), dim = F::add(w.im, u.im);

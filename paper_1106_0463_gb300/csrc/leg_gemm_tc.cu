@@ -538,27 +538,27 @@ __device__ __forceinline__ void split_pair(float ha, float la, float hb, float l
     o[6] = __floats2half2_rn(da * ISC, db * ISC);
 }
 
-template <class T, bool STAGE>
+template <class T, bool STAGE, int NT = SPLIT_THREADS>
 __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
                                           size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00, int fbits)
 {
     const float SC = __int_as_float((127 + fbits) << 23), ISC = __int_as_float((127 - fbits) << 23);
-    __shared__ float red[SPLIT_THREADS / 32];
+    __shared__ float red[NT / 32];
     __shared__ int s_e;
     extern __shared__ __align__(16) unsigned char split_smem[];
     T *xs = reinterpret_cast<T *>(split_smem);   // STAGE: np values, zero beyond n
     float m = 0.0f;
-    for (int base = 0; base < np; base += SPLIT_THREADS * SPLIT_U) {
+    for (int base = 0; base < np; base += NT * SPLIT_U) {
         T t[SPLIT_U];
 #pragma unroll
         for (int u = 0; u < SPLIT_U; ++u) {
-            const int k = base + u * SPLIT_THREADS + threadIdx.x;
+            const int k = base + u * NT + threadIdx.x;
             t[u] = (k < n) ? row[k] : zero_of<T>();
         }
 #pragma unroll
         for (int u = 0; u < SPLIT_U; ++u) {
             m = fmaxf(m, fabsf(hi_of(t[u])));
-            const int k = base + u * SPLIT_THREADS + threadIdx.x;
+            const int k = base + u * NT + threadIdx.x;
             if (STAGE && k < np) xs[k] = t[u];
         }
     }
@@ -568,7 +568,7 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     __syncthreads();
     if (threadIdx.x == 0) {
         float mm = 0.0f;
-        for (int w = 0; w < SPLIT_THREADS / 32; ++w) mm = fmaxf(mm, red[w]);
+        for (int w = 0; w < NT / 32; ++w) mm = fmaxf(mm, red[w]);
         int e = 0;
         if (mm > 0.0f) {
             const float fr = frexpf(mm, &e);   // mm = fr 2^e, fr in [0.5, 1)
@@ -591,7 +591,7 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     // x 2^-e: one exact multiply while 2^-e is a normal float (ldexpf beyond)
     const bool mul_ok = (-e >= -126 && -e <= 127);
     const float sc = mul_ok ? __int_as_float((127 - e) << 23) : 0.0f;
-    for (int c = threadIdx.x; c < np / 8; c += SPLIT_THREADS) {
+    for (int c = threadIdx.x; c < np / 8; c += NT) {
         float h[8], l[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
@@ -616,12 +616,12 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     }
 }
 
-template <class T, bool STAGE>
-__global__ void __launch_bounds__(SPLIT_THREADS) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
-                                                                   LegSplitIn in, float2 *G, int ldg, float2 a00)
+template <class T, bool STAGE, int NT>
+__global__ void __launch_bounds__(NT) split_rows_kernel(const T *__restrict__ x, int ldx, int n, int np,
+                                                        LegSplitIn in, float2 *G, int ldg, float2 a00)
 {
     const int b = blockIdx.x;
-    split_row<T, STAGE>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
+    split_row<T, STAGE, NT>(x + (size_t)b * ldx, n, np, in.base + (size_t)b * in.ld, in.pstride, in.fexp + b,
                         G ? G + (size_t)b * ldg : nullptr, a00, in.fbits);
     leg_griddep_trigger();   // after this CTA's stores: the GEMM's setup may start
 }
@@ -643,8 +643,25 @@ __global__ void __launch_bounds__(SPLIT_THREADS) split_ragged_kernel(const float
     leg_griddep_trigger();
 }
 
-// Rows of at most this many bytes are staged in shared memory by the split.
-constexpr size_t SPLIT_STAGE_MAX = 16384;
+// Rows of at most this many bytes are staged in shared memory by the split
+// (below the 48 KB a CTA gets without opting in).
+constexpr size_t SPLIT_STAGE_MAX = 40960;
+// Rows of at least this many (padded) elements are split by CTAs of
+// SPLIT_THREADS_LONG threads: with one CTA per row, a batch of a few hundred
+// long rows leaves the SMs too few loads in flight at 128 threads.
+constexpr int SPLIT_LONG_NP = 4096;
+constexpr int SPLIT_THREADS_LONG = 512;
+
+template <class T, int NT>
+void split_rows_launch(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 *G, int ldg, float2 a00p,
+                       int B, cudaStream_t st)
+{
+    const size_t bytes = ((size_t)np * sizeof(T) + 15) / 16 * 16;
+    if (bytes <= SPLIT_STAGE_MAX)
+        split_rows_kernel<T, true, NT><<<B, NT, bytes, st>>>(x, ldx, n, np, in, G, ldg, a00p);
+    else
+        split_rows_kernel<T, false, NT><<<B, NT, 0, st>>>(x, ldx, n, np, in, G, ldg, a00p);
+}
 
 template <class T>
 int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 *G, int ldg, double a00, int B,
@@ -653,11 +670,10 @@ int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 
     if (B == 0) return LEG_OK;
     const float ah = (float)a00;
     const float2 a00p = make_float2(ah, (float)(a00 - (double)ah));
-    const size_t bytes = ((size_t)np * sizeof(T) + 15) / 16 * 16;
-    if (bytes <= SPLIT_STAGE_MAX)
-        split_rows_kernel<T, true><<<B, SPLIT_THREADS, bytes, st>>>(x, ldx, n, np, in, G, ldg, a00p);
+    if (np >= SPLIT_LONG_NP)
+        split_rows_launch<T, SPLIT_THREADS_LONG>(x, ldx, n, np, in, G, ldg, a00p, B, st);
     else
-        split_rows_kernel<T, false><<<B, SPLIT_THREADS, 0, st>>>(x, ldx, n, np, in, G, ldg, a00p);
+        split_rows_launch<T, SPLIT_THREADS>(x, ldx, n, np, in, G, ldg, a00p, B, st);
     LEG_LAUNCH_CHECK("split_rows_kernel");
     return LEG_OK;
 }
