@@ -118,7 +118,11 @@ template <int NPROD> __host__ __device__ constexpr int max_tn() { return NPROD >
 __device__ __forceinline__ uint32_t acc1_col(int tn, int b) { return (uint32_t)(tn * (2 + b)); }
 
 // Pair tile t of a launch: its problem, first operator row j0, first function b0.
-// Row tiles vary fastest, so concurrent pairs share their input tiles in L2.
+// The tiles of a problem are ordered so that the pairs running at the same time
+// share the larger operand's tiles in L2: row tiles vary fastest when the input
+// planes outweigh the operator planes (each input tile is then read from DRAM
+// once), function tiles when the operator does (each operator tile is read
+// once while the input planes stay in L2).
 __device__ __forceinline__ const TcProblem &tile_problem(const TcProblem &single, const TcProblem *multi,
                                                          int nprob, int t, int tn, int &j0, int &b0)
 {
@@ -130,8 +134,13 @@ __device__ __forceinline__ const TcProblem &tile_problem(const TcProblem &single
         pr = &multi[p];
         lt = t - pr->tile0;
     }
-    j0 = (lt % pr->ntm) * PAIR_M;
-    b0 = (lt / pr->ntm) * tn;
+    if (pr->fn_fast) {
+        b0 = (lt % pr->ntn) * tn;
+        j0 = (lt / pr->ntn) * PAIR_M;
+    } else {
+        j0 = (lt % pr->ntm) * PAIR_M;
+        b0 = (lt / pr->ntm) * tn;
+    }
     return *pr;
 }
 
@@ -881,8 +890,9 @@ int choose_tn(int ntm, int B, int nkb, int pairs, int maxtn = 128)
     return best;
 }
 
+// na, nf: operator and input planes of the problem (their bytes set the tile order).
 void finish_problem(TcProblem *pr, const int *aexp, const int *fexp, void *out, int ldo, int rows, int B, int Kc,
-                    int tn)
+                    int tn, int na, int nf)
 {
     pr->aexp = aexp;
     pr->fexp = fexp;
@@ -895,6 +905,7 @@ void finish_problem(TcProblem *pr, const int *aexp, const int *fexp, void *out, 
     pr->ntm = ceil_div(rows, PAIR_M);
     pr->ntn = ceil_div(B, tn);
     pr->tile0 = 0;
+    pr->fn_fast = (long long)na * rows > (long long)nf * B ? 1 : 0;
     pr->w1 = 1.0f;
 }
 
@@ -906,7 +917,7 @@ int make_split(TcProblem *pr, const __half *a0, size_t apstride, int rows, int l
     int rc;
     if ((rc = make_map(&pr->a, a0, Kc, rows, lda, LEG_SPLIT_NA, apstride, false, CTA_M))) return rc;
     if ((rc = make_map(&pr->f, in.base, Kc, B, in.ld, LEG_SPLIT_NF, in.pstride, false, tn / 2))) return rc;
-    finish_problem(pr, aexp, in.fexp, out, ldo, rows, B, Kc, tn);
+    finish_problem(pr, aexp, in.fexp, out, ldo, rows, B, Kc, tn, LEG_SPLIT_NA, LEG_SPLIT_NF);
     pr->w1 = ldexpf(1.0f, -in.fbits);
     return LEG_OK;
 }
@@ -1052,7 +1063,7 @@ int leg_gemm_bf16_fwd(leg_plan *p, int B, void *out, int ldo, cudaStream_t st)
     memset(&pr, 0, sizeof(pr));
     if ((rc = make_map(&pr.a, p->Abf, p->Kp, rows, p->Kp, 1, (size_t)rows * p->Kp, true, CTA_M))) return rc;
     if ((rc = make_map(&pr.f, p->Fbf, p->Kp, B, p->Kp, 1, (size_t)B * p->Kp, true, tn / 2))) return rc;
-    finish_problem(&pr, nullptr, nullptr, out, ldo, rows, B, p->Kp, tn);
+    finish_problem(&pr, nullptr, nullptr, out, ldo, rows, B, p->Kp, tn, 1, 1);
     return launch_tc<1, false>(pr, nullptr, 1, tiles_of(pr), tn, p->status, p->wait_limit, st);
 }
 

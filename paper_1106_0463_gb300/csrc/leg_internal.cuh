@@ -214,6 +214,7 @@ struct TcProblem {
     int tn;                  // functions per pair tile (multiple of 16, <= 256)
     int ntm, ntn;            // tiles along rows (256 each) and along functions (tn each)
     int tile0;               // first global tile index of this problem (grouped launches)
+    int fn_fast;             // 1: function tiles vary fastest in the tile order (operator-heavy problems)
     float w1;                // 2^-s: weight of acc1 and acc2 (split path)
 };
 
