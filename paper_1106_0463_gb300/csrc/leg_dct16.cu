@@ -47,7 +47,7 @@ __device__ __forceinline__ void dct16(CxT<R> *buf, typename Fa<R>::T *wsum, int 
             yy[u] = F::sub(F::half(F::add(xj, xl)), F::mul(s, d));
             if (j >= 1 && j < L / 2) part = F::add(part, F::mul(c, d));
         }
-        v[b] = {F::norm(yy[0]), F::norm(yy[1])};
+        v[b] = {yy[0], yy[1]};
     }
     const T_ x1 = F::norm(F::add(F::sub(load(0), load(L)), F::pow2(fn_sum<R, LOG2H, XE>(part, t, wsum), 1)));
     fsync<T>();   // load() may read buf (the staged row): all reads precede the first pass's writes

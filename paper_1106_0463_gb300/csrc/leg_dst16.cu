@@ -68,8 +68,8 @@ __device__ __forceinline__ void dst16(CxT<R> *buf, int t, const typename Ar<R>::
         T_ c, s;
         twid(tw, 2 * k, c, s);   // e^{2 pi i k / L}
         // i e^{2 pi i k/L} (dre + i dim) = -(s dre + c dim) + i (c dre - s dim)
-        v[b] = {F::norm(F::sub(pre, F::add(F::mul(s, dre), F::mul(c, dim)))),
-                F::norm(F::add(pim, F::sub(F::mul(c, dre), F::mul(s, dim))))};
+        v[b] = {F::sub(pre, F::add(F::mul(s, dre), F::mul(c, dim))),
+                F::add(pim, F::sub(F::mul(c, dre), F::mul(s, dim)))};
     }
     fsync<T>();   // load() reads buf (the staged row): all reads precede the first pass's writes
     // 2. FFT of length H

@@ -547,6 +547,55 @@ __device__ __forceinline__ void split_pair(float ha, float la, float hb, float l
     o[6] = __floats2half2_rn(da * ISC, db * ISC);
 }
 
+// Power of two e of a row's scale: max |x| 2^-e <= 1 (0 for a zero row).
+__device__ __forceinline__ int split_scale_exp(float mm)
+{
+    int e = 0;
+    if (mm > 0.0f) {
+        const float fr = frexpf(mm, &e);   // mm = fr 2^e, fr in [0.5, 1)
+        if (fr == 0.5f) e -= 1;            // scaled |hi| <= 1, hence |F0| <= 1
+    }
+    return e;
+}
+
+// a00 x[0] as a double-float pair (a00 = hi + lo; x[0] is FP32): exact
+// product of the leading parts by FMA, the rest in FP32
+__device__ __forceinline__ float2 split_g0(float x, float2 a00)
+{
+    const float p = x * a00.x;
+    const float q = fmaf(x, a00.x, -p) + x * a00.y;
+    const float h = p + q;
+    return make_float2(h, q - (h - p));
+}
+
+// The seven planes of the 8 values v[0..7] of a row scaled by 2^-e, one
+// 16-byte store per plane at P + p pstride.
+template <class T>
+__device__ __forceinline__ void split_planes8(const T (&v)[8], int e, float SC, float ISC, __half *__restrict__ P,
+                                              size_t pstride)
+{
+    // x 2^-e: one exact multiply while 2^-e is a normal float (ldexpf beyond)
+    const bool mul_ok = (-e >= -126 && -e <= 127);
+    const float sc = mul_ok ? __int_as_float((127 - e) << 23) : 0.0f;
+    float h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        h[i] = mul_ok ? hi_of(v[i]) * sc : ldexpf(hi_of(v[i]), -e);
+        l[i] = mul_ok ? lo_of(v[i]) * sc : ldexpf(lo_of(v[i]), -e);
+    }
+    __align__(16) __half2 o[LEG_SPLIT_NF][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        __half2 q[LEG_SPLIT_NF];
+        split_pair(h[2 * i], l[2 * i], h[2 * i + 1], l[2 * i + 1], SC, ISC, q);
+#pragma unroll
+        for (int p = 0; p < LEG_SPLIT_NF; ++p) o[p][i] = q[p];
+    }
+#pragma unroll
+    for (int p = 0; p < LEG_SPLIT_NF; ++p)
+        *reinterpret_cast<uint4 *>(P + p * pstride) = *reinterpret_cast<const uint4 *>(o[p]);
+}
+
 template <class T, bool STAGE, int NT = SPLIT_THREADS>
 __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int np, __half *__restrict__ P,
                                           size_t pstride, int *__restrict__ xexp, float2 *g0, float2 a00, int fbits)
@@ -578,50 +627,23 @@ __device__ __forceinline__ void split_row(const T *__restrict__ row, int n, int 
     if (threadIdx.x == 0) {
         float mm = 0.0f;
         for (int w = 0; w < NT / 32; ++w) mm = fmaxf(mm, red[w]);
-        int e = 0;
-        if (mm > 0.0f) {
-            const float fr = frexpf(mm, &e);   // mm = fr 2^e, fr in [0.5, 1)
-            if (fr == 0.5f) e -= 1;            // scaled |hi| <= 1, hence |F0| <= 1
-        }
+        const int e = split_scale_exp(mm);
         s_e = e;
         *xexp = e;
     }
     __syncthreads();
     const int e = s_e;
-    if (g0 && threadIdx.x == 32) {
-        // a00 x[0] as a double-float pair (a00 = hi + lo; x[0] is FP32): exact
-        // product of the leading parts by FMA, the rest in FP32
-        const float x = hi_of(STAGE ? xs[0] : row[0]);
-        const float p = x * a00.x;
-        const float q = fmaf(x, a00.x, -p) + x * a00.y;
-        const float h = p + q;
-        *g0 = make_float2(h, q - (h - p));
-    }
-    // x 2^-e: one exact multiply while 2^-e is a normal float (ldexpf beyond)
-    const bool mul_ok = (-e >= -126 && -e <= 127);
-    const float sc = mul_ok ? __int_as_float((127 - e) << 23) : 0.0f;
+    if (g0 && threadIdx.x == 32) *g0 = split_g0(hi_of(STAGE ? xs[0] : row[0]), a00);
     for (int c = threadIdx.x; c < np / 8; c += NT) {
-        float h[8], l[8];
+        T v[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int k = 8 * c + i;
-            T v = zero_of<T>();
-            if (STAGE) v = xs[k];                 // zero-padded: no bound check
-            else if (k < n) v = row[k];
-            h[i] = mul_ok ? hi_of(v) * sc : ldexpf(hi_of(v), -e);
-            l[i] = mul_ok ? lo_of(v) * sc : ldexpf(lo_of(v), -e);
+            v[i] = zero_of<T>();
+            if (STAGE) v[i] = xs[k];                 // zero-padded: no bound check
+            else if (k < n) v[i] = row[k];
         }
-        __align__(16) __half2 o[LEG_SPLIT_NF][4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            __half2 q[LEG_SPLIT_NF];
-            split_pair(h[2 * i], l[2 * i], h[2 * i + 1], l[2 * i + 1], SC, ISC, q);
-#pragma unroll
-            for (int p = 0; p < LEG_SPLIT_NF; ++p) o[p][i] = q[p];
-        }
-#pragma unroll
-        for (int p = 0; p < LEG_SPLIT_NF; ++p)
-            *reinterpret_cast<uint4 *>(P + p * pstride + 8 * c) = *reinterpret_cast<const uint4 *>(o[p]);
+        split_planes8<T>(v, e, SC, ISC, P + 8 * c, pstride);
     }
 }
 
@@ -672,6 +694,8 @@ void split_rows_launch(const T *x, int ldx, int n, int np, const LegSplitIn &in,
         split_rows_kernel<T, false, NT><<<B, NT, 0, st>>>(x, ldx, n, np, in, G, ldg, a00p);
 }
 
+// FP32 rows of at least SPLIT_LONG_NP elements whose padded length splits into
+// SPLIT_CL segments of whole 8-element groups go to clusters of SPLIT_CL CTAs.
 template <class T>
 int split_rows(const T *x, int ldx, int n, int np, const LegSplitIn &in, float2 *G, int ldg, double a00, int B,
                cudaStream_t st)
