@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--workload", default=HEADLINE)
     ap.add_argument("--path", default="split_fp16", choices=["split_fp16", "f32", "bf16", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-route2", action="store_true",
+                    help="also time oracle route 2 with explicit operators at B=4096, K=1025 (the build takes minutes)")
     ap.add_argument("--no-extras", action="store_true", help="headline workload only")
     ap.add_argument("--tile", type=int, default=None,
                     help="GEMM tile width of the headline plan (0 = the library's model); with --transform, "
@@ -203,6 +205,30 @@ def oracle_rate(name: str, seconds: float = 10.0, max_fns: int = 256):
     return {"value": n * cfg["N"] / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
             "sample": "%d of %d functions of %s, oracle %s, FP64, OpenMP, %.2f s"
                       % (n, cfg["B"], name, oracle_route_name(name), dt)}, n, dt
+
+
+def oracle_route2_operator_rate(name: str):
+    """Route 2 with its explicit operators built once (not timed): C = (F A^T) R^T
+    for the whole batch by the BLAS behind numpy, A the M x K Abel-interpolation
+    operator and R the N x M twisted Fourier sum (Eqs. 2.4, 2.5)."""
+    from oracle import oracle as O
+    cfg = workloads.CONFIGS[name]
+    f = workloads.workload_inputs(name).astype(np.float64)
+    Q = O.exact_tau_points(cfg["K"])
+    t0 = time.time()
+    A = O.abel_operator(cfg["M"], cfg["K"], Q)
+    R = O.twisted_dft_matrix(cfg["N"], cfg["M"])
+    build = time.time() - t0
+    (f[:64] @ A.T) @ R.T
+    t0 = time.perf_counter()
+    C = (f @ A.T) @ R.T
+    dt = time.perf_counter() - t0
+    ref = oracle_coeffs(O, name, f[:2])
+    return {"value": cfg["B"] * cfg["N"] / dt, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "sample": "all %d functions of %s, oracle route 2 with the explicit operators A (%d x %d) and R "
+                      "(%d x %d) built once in %.1f s (not timed): C = (F A^T) R^T by numpy's BLAS, %.3f s"
+                      % (cfg["B"], name, cfg["M"], cfg["K"], cfg["N"], cfg["M"], build, dt),
+            "max_rel_diff_vs_route1": relerr(C[:2], ref)}
 
 
 def reference_arm(args, rank, world):
@@ -364,7 +390,8 @@ def fft_roofline(B, M, N, rows, path, fft_ms, peaks, peak_src, traffic, name, si
 
 # ------------------------------------------------------------------ GPU helpers
 def time_steps(torch, fn, flush, steps, warmup, clocks=None):
-    """CUDA-event times (ms) of fn() over `steps` calls, L2 flushed before each."""
+    """CUDA-event times (ms) of fn() over `steps` calls, L2 flushed before each
+    (flush None: L2 left warm)."""
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
@@ -373,7 +400,8 @@ def time_steps(torch, fn, flush, steps, warmup, clocks=None):
         clocks.wait_first()
     ts = []
     for _ in range(steps):
-        flush.zero_()
+        if flush is not None:
+            flush.zero_()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         fn()
@@ -458,7 +486,8 @@ class Dense:
             return self.f64
         return self.f32
 
-    def run(self, path, flush, steps, warmup, peaks, peak_src, clocks=None, transform=None, stages=10):
+    def run(self, path, flush, steps, warmup, peaks, peak_src, clocks=None, transform=None, stages=10,
+            warm_steps=0):
         leg, torch = self.leg, self.torch
         plan = self.plan(path)
         prev = plan.transform
@@ -472,6 +501,20 @@ class Dense:
         for _ in range(min(stages, steps)):
             flush.zero_()
             st.append(plan.forward_profiled(f, c))
+        warm = None
+        if warm_steps:
+            # back to back between one event pair: no flush, no host gap between steps
+            for _ in range(2):
+                plan.forward(f, c)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(warm_steps):
+                plan.forward(f, c)
+            e1.record()
+            e1.synchronize()
+            tw = e0.elapsed_time(e1) / warm_steps
+            warm = {"value": self.B * self.N / (tw / 1e3), "ms_per_step": tw, "steps": warm_steps,
+                    "l2": "not flushed; steps back to back between one pair of events"}
         plan.status()
         ms = float(np.mean(ts))
         prep_ms, gemm_ms, fft_ms = (float(v) for v in np.mean(np.array(st), 0))
@@ -483,6 +526,8 @@ class Dense:
                "transform_roofline": fft_roofline(self.B, self.M, self.N, self.rows, path, fft_ms, peaks, peak_src,
                                                   TRAFFIC, self.name, sine=plan.transform == leg.TRANSFORM_SINE),
                "gpu_launches_per_step": LAUNCHES[path]}
+        if warm is not None:
+            out["l2_warm"] = warm
         if self.ref is not None:
             got = c[torch.from_numpy(self.sample).cuda()].double().cpu().numpy()
             out["max_rel_err"] = relerr(got, self.ref)
@@ -780,7 +825,8 @@ def gpu_arm(args, rank, world, local_rank):
     barrier()
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     phys = vis.split(",")[local_rank].strip() if vis else str(local_rank)
-    res = head.run(args.path, flush, args.steps, args.warmup, peaks, peak_src, clocks=ClockSampler(phys))
+    res = head.run(args.path, flush, args.steps, args.warmup, peaks, peak_src, clocks=ClockSampler(phys),
+                   warm_steps=min(args.steps, 50))
     barrier()
     total_ms = max_over_ranks(torch, dist, float(np.sum(res["_ts"])), "cuda")
     ms_per_step = total_ms / args.steps
@@ -833,6 +879,7 @@ def gpu_arm(args, rank, world, local_rank):
         "roofline": roof, "stages_ms": res["stages_ms"],
         "transform_roofline": res["transform_roofline"], "plan_build_s": head.plan_s.get(args.path),
         "e2e": e2e, "clocks": res["_clk"], "gpu_launches": LAUNCHES[args.path] * args.steps,
+        "l2_warm": res.get("l2_warm"),
     }
     wl = {}
     if not args.no_extras:
@@ -854,7 +901,7 @@ def gpu_arm(args, rank, world, local_rank):
         c2name = "cheb_b4096_k1025_n512_m2048"
         c2 = Dense(leg, torch, c2name, rank, with_ref, extra=24)
         sub = {}
-        sub["split_fp16"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src))
+        sub["split_fp16"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src, warm_steps=50))
         sub["split_fp16_sine_form"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src,
                                                    transform=leg.TRANSFORM_SINE))
         sub["f32"] = strip(c2.run("f32", flush, 20, 3, peaks, peak_src))
@@ -870,6 +917,8 @@ def gpu_arm(args, rank, world, local_rank):
         if c2.ref is not None:
             sub["collapsed_split_fp16"]["max_rel_err"] = relerr(
                 cc[torch.from_numpy(c2.sample).cuda()].double().cpu().numpy(), c2.ref)
+        if rank == 0 and args.cpu_route2:   # minutes of CPU time for the operator build
+            sub["cpu_baseline_route2_explicit_operator"] = oracle_route2_operator_rate(c2name)
         wl[c2name] = sub
         del c2, coll
         wl["ragged_10000"] = ragged(leg, torch, flush, rank, peaks, peak_src, with_ref)
