@@ -333,8 +333,8 @@ def gemm_roofline(B, rows, K, Kp, path, gemm_ms, peaks, peak_src, traffic, name)
     Eq. 2.12) over the CUDA-event stage time against the measured dense
     tensor peak; executed FLOP of the split products and the algorithmic HBM
     bytes (operator planes, input planes, G) beside it."""
-    hbm = peaks.get("hbm_gbs", 6767.1)
-    peak = peaks.get("bf16_tflops", 1880.7)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    peak = peaks.get("bf16_tflops", 1900.0)
     useful = 2.0 * B * rows * K
     gemm_rows = rows - 1 if path == "split_fp16" else rows   # split: row 0 is a00 e_0, done by the split
     executed = PRODUCTS[path] * 2.0 * B * gemm_rows * Kp
@@ -366,7 +366,7 @@ def gemm_roofline(B, rows, K, Kp, path, gemm_ms, peaks, peak_src, traffic, name)
 def fft_roofline(B, M, N, rows, path, fft_ms, peaks, peak_src, traffic, name, sine=False):
     """The transform stage: bound by FP32 (double-float) or FP64 arithmetic at
     the precision the split / FP64 paths need, by HBM for the FP32 path."""
-    hbm = peaks.get("hbm_gbs", 6767.1)
+    hbm = peaks.get("hbm_gbs", 6800.0)
     gbytes = {"split_fp16": 8, "f64": 8, "f32": 4, "bf16": 4}[path]
     bytes_ = B * rows * gbytes + B * N * (8 if path == "f64" else 4)
     sec = fft_ms / 1e3
@@ -643,7 +643,7 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
         useful += 2.0 * Bb * rows * K
         executed += 8 * 2.0 * Bb * (rows - 1) * Kp
         abytes += 3 * (rows - 1) * Kp * 2 + 7 * Bb * Kp * 2 + Bb * rows * 8
-    peak = peaks.get("bf16_tflops", 1880.7)
+    peak = peaks.get("bf16_tflops", 1900.0)
     sec = gemm_ms / 1e3
     roof = {"kernel": "tc_gemm_kernel (grouped Abel GEMM over all buckets)", "bound": "tensor",
             "achieved": useful / sec / 1e12, "peak": peak, "unit": "TFLOP/s", "frac": useful / sec / 1e12 / peak,
