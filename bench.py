@@ -892,6 +892,27 @@ def gpu_arm(args, rank, world, local_rank):
             sweep[p] = {"value": r["value"], "ms_per_step": r["ms_per_step"], "max_rel_err": r.get("max_rel_err"),
                         "stages_ms": r["stages_ms"]}
         wl["precision_sweep_" + name] = sweep
+        if args.path == "split_fp16":
+            # ablation: the collapsed operator L = R A (N x K, built once in FP64) in one
+            # split GEMM with no transform, on the same inputs
+            t0 = time.time()
+            coll = leg.Plan(N, head.M, head.K, 0, leg.SPLIT_FP16, flags=leg.FLAG_COLLAPSED)
+            torch.cuda.synchronize()
+            build_s = time.time() - t0
+            fin = head.inputs("split_fp16")
+            cc = torch.empty((B, N), dtype=torch.float32, device="cuda")
+            ts, _ = time_steps(torch, lambda: coll.forward(fin, cc), flush, 20, 3)
+            coll.status()
+            ms = float(np.mean(ts))
+            ent = {"value": B * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "launches_per_step": 2,
+                   "plan_build_s": build_s,
+                   "useful_gemm_tflops": 2.0 * B * N * head.K / (ms / 1e3) / 1e12,
+                   "note": "ablation, not the paper's route: L = R A multiplied out at plan time"}
+            if head.ref is not None:
+                ent["max_rel_err"] = relerr(cc[torch.from_numpy(head.sample).cuda()].double().cpu().numpy(),
+                                            head.ref)
+            wl["collapsed_split_fp16_" + name] = ent
+            del coll
         line["speedup_vs_fp64_gpu_path"] = (value / world) / sweep["f64"]["value"]
         other = leg.TRANSFORM_REG if tuned["fft"] == leg.TRANSFORM_SINE else leg.TRANSFORM_SINE
         r = head.run(args.path, flush, 20, 3, peaks, peak_src, transform=other)
