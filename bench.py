@@ -901,11 +901,12 @@ def gpu_arm(args, rank, world, local_rank):
             build_s = time.time() - t0
             fin = head.inputs("split_fp16")
             cc = torch.empty((B, N), dtype=torch.float32, device="cuda")
+            coll_tile = coll.autotune(fin)   # the GEMM tile width, timed on this batch
             ts, _ = time_steps(torch, lambda: coll.forward(fin, cc), flush, 20, 3)
             coll.status()
             ms = float(np.mean(ts))
             ent = {"value": B * N / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "launches_per_step": 2,
-                   "plan_build_s": build_s,
+                   "plan_build_s": build_s, "tuned": coll_tile,
                    "useful_gemm_tflops": 2.0 * B * N * head.K / (ms / 1e3) / 1e12,
                    "note": "ablation, not the paper's route: L = R A multiplied out at plan time"}
             if head.ref is not None:
