@@ -287,8 +287,8 @@ ALU_PEAK_TOPS = {"f32": 152 * 128 * 2.07e9 / 1e12, "f64": 1.25}
 # (one ncu capture per kernel, summaries under profiles/); keyed by
 # (stage, path, workload).  A kernel changed since its capture has no entry.
 TRAFFIC = {
-    ("abel_gemm", "split_fp16", "cheb_b256_k8193_n4096_m16384"): 441985024,   # tc_gemm_pair_split_fp16_cheb_b256_...
-    ("fft_sine", "split_fp16", "cheb_b256_k8193_n4096_m16384"): 17057792,     # dst16_forward_dfl_cheb_b256_...
+    ("abel_gemm", "split_fp16", "cheb_b256_k8193_n4096_m16384"): 441804032,   # tc_gemm_pair_split_fp16_cheb_b256_...
+    ("fft_sine", "split_fp16", "cheb_b256_k8193_n4096_m16384"): 17057024,     # dst16_forward_dfl_cheb_b256_...
     ("abel_gemm", "split_fp16", "ragged"): 628728064,                          # tc_gemm_grouped_split_fp16_ragged_10000
 }
 
