@@ -391,14 +391,16 @@ def fft_roofline(B, M, N, rows, path, fft_ms, peaks, peak_src, traffic, name, si
 # ------------------------------------------------------------------ GPU helpers
 def time_steps(torch, fn, flush, steps, warmup, clocks=None):
     """CUDA-event times (ms) of fn() over `steps` calls, L2 flushed before each
-    (flush None: L2 left warm)."""
+    (flush None: L2 left warm).  All steps are queued before one synchronise,
+    so the device never waits for the host inside a timed interval (a host
+    stall between an event and the launches after it would be counted)."""
     for _ in range(warmup):
         fn()
     torch.cuda.synchronize()
     if clocks is not None:
         clocks.start()
         clocks.wait_first()
-    ts = []
+    evs = []
     for _ in range(steps):
         if flush is not None:
             flush.zero_()
@@ -406,8 +408,9 @@ def time_steps(torch, fn, flush, steps, warmup, clocks=None):
         e0.record()
         fn()
         e1.record()
-        e1.synchronize()
-        ts.append(e0.elapsed_time(e1))
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    ts = [e0.elapsed_time(e1) for e0, e1 in evs]
     clk = clocks.stop() if clocks is not None else None
     return ts, clk
 
@@ -683,7 +686,7 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
     return out
 
 
-def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref):
+def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3):
     """B=1024, K=4097, N=2048, M=8192: forward + backward of the split path
     (leg_forward, leg_backward) against the FP64 GPU path, errors of both
     directions against the oracle (route 1 and route 1 transposed)."""
@@ -699,13 +702,14 @@ def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref):
     v = torch.from_numpy(v_np).cuda()
     df = torch.empty_like(x)
     split.reserve(B)
+    tuned = split.autotune(x)   # the forward's GEMM tile width and transform kernel, timed on this batch
 
     def fwd_bwd():
         split.forward(x, c)
         split.backward(v, df)
-    ts, _ = time_steps(torch, fwd_bwd, flush, 20, 3)
-    tf, _ = time_steps(torch, lambda: split.forward(x, c), flush, 20, 3)
-    tb, _ = time_steps(torch, lambda: split.backward(v, df), flush, 20, 3)
+    ts, _ = time_steps(torch, fwd_bwd, flush, steps, warmup)
+    tf, _ = time_steps(torch, lambda: split.forward(x, c), flush, steps, warmup)
+    tb, _ = time_steps(torch, lambda: split.backward(v, df), flush, steps, warmup)
     split.status()
     x64, v64 = x.double(), v.double()
     c64 = torch.empty((B, N), dtype=torch.float64, device="cuda")
@@ -720,6 +724,7 @@ def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref):
            "forward_ms": float(np.mean(tf)), "backward_ms": float(np.mean(tb)),
            "f64_gpu_path": {"value": B * N / (ms64 / 1e3), "ms_per_step": ms64},
            "speedup_vs_fp64_gpu_path": ms64 / ms, "plan_build_s": d.plan_s.get("split_fp16"),
+           "tuned": {"tn": tuned["tn"], "transform": TRANSFORM_NAMES[tuned["fft"]]},
            "gpu_launches_per_step": 3 + 3}
     if with_ref:
         from oracle import oracle as O
@@ -783,6 +788,26 @@ def ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
         dist.destroy_process_group()
 
 
+def differentiation_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
+    """--workload diff_b1024_k4097: forward + backward (leg_forward, leg_backward)
+    at B=1024, K=4097, N=2048, M=8192 as the timed workload."""
+    r = differentiation(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup)
+    ms = max_over_ranks(torch, dist, r["ms_per_step"], "cuda")
+    if rank == 0:
+        line = {"metric": METRIC + " (forward + backward)", "value": whole_job_rate(world, 1024 * 2048, ms),
+                "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_STR["split_fp16"],
+                "data": "synthetic",
+                "config": {"workload": "cheb_b1024_k4097_n2048_m8192", "B": 1024, "K": 4097, "N": 2048, "M": 8192,
+                           "step": "forward + backward", "l2": "flushed (512 MiB write) before every timed step"},
+                "gpu_launches": r["gpu_launches_per_step"] * args.steps}
+        line.update({k: r[k] for k in r if k not in ("value", "unit", "ms_per_step", "gpu_launches_per_step")})
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def gpu_arm(args, rank, world, local_rank):
     import torch
     import paper_1106_0463_gb300 as leg
@@ -798,6 +823,9 @@ def gpu_arm(args, rank, world, local_rank):
     with_ref = rank == 0
     if name == "ragged_10000":
         ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src)
+        return
+    if name == "diff_b1024_k4097":
+        differentiation_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src)
         return
 
     def barrier():

@@ -160,17 +160,24 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dct16_a
     const int f = min(blockIdx.x * D::FPB + grp, B - 1);
     const bool live = blockIdx.x * D::FPB + grp < B;
     const VIN *vf = v + (size_t)f * N;
+    // w_n = (2n+1) v_n staged in the exchange buffer (N <= L values of the
+    // arithmetic type fit in its 2L words), read by the fold below: coalesced
+    // loads of the row once, then x_n = w_n - w_{n-1} from shared memory
+    T_ *ws = reinterpret_cast<T_ *>(buf);
+    for (int n = t; n < N; n += D::T) ws[n] = F::mul(F::of_int(2 * n + 1), in_of<R>(vf[n]));
+    fsync<D::T>();
     auto load = [&](int n) -> T_ {
         if (n > N) return F::zero();
         T_ x = F::zero();
-        if (n < N) x = F::mul(F::of_int(2 * n + 1), in_of<R>(vf[n]));
-        if (n >= 1) x = F::sub(x, F::mul(F::of_int(2 * n - 1), in_of<R>(vf[n - 1])));
+        if (n < N) x = ws[n];
+        if (n >= 1) x = F::sub(x, ws[n - 1]);
         return x;
     };
+    // x_0 and x_L before the transform overwrites the staged values
+    const T_ x0 = load(0), xL = load(L);
     dct16<R, LOG2H, LEG_DCT16_LOG2E>(buf, wsum, t, tw, D::H - 1, load);
     if (!live) return;
     const T_ *Xs = reinterpret_cast<const T_ *>(buf);
-    const T_ x0 = load(0), xL = load(L);
     for (int j = t; j <= L; j += D::T) {
         const T_ s = F::add(Xs[D::px(j)], F::add(x0, (j & 1) ? F::neg(xL) : xL));
         const int e = (j == 0 || j == L) ? -(LOG2H + 3) : -(LOG2H + 2);
