@@ -117,6 +117,114 @@ __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE
     }
 }
 
+// The exact adjoint of the sine-form map above (v -> gbar = S^T v, S the map
+// from a row of G to c), step by step in reverse order (each step's transpose
+// for the real inner product, complex values as pairs):
+//   zbar_i(n) = (-1)^n (2n+1) v_n / M (zero for the i no n < N reaches);
+//   conj(zetabar_m) = zbar_2m - i zbar_2m+1;
+//   Ybar = conj(FFT_H(conj(zetabar))) (positive exponent: the transpose of the
+//   forward FFT is the negative-exponent DFT);
+//   Wbar_k = conj(1 + i e_k) Ybar_k + (1 - i e_{H-k}) conj(Ybar_{H-k}),
+//   e_k = e^{2 pi i k / L}, e_{H-k} = -conj(e_k) (0 < k < H);
+//   Wbar_0 = (1 - i) Ybar_0, Wbar_H = (1 - i) conj(Ybar_0);
+//   gbar_k = (1 - c_k) Re Wbar_k - s_k Im Wbar_k, gbar_{L-k} = (1 + c_k) Re Wbar_k
+//   + s_k Im Wbar_k with (c_k, s_k) = e^{2 pi i k / M} (0 < k < H);
+//   gbar_L = 2 Re Wbar_0, gbar_H = 2 Re Wbar_H, gbar_0 = 0 (g_0 does not
+//   enter the sine form: phi vanishes at y = 0).
+// Every gbar index receives exactly one of these terms, so each thread writes
+// its own outputs.
+template <class R, class VIN, int LOG2H>
+__global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dst16_adjoint_kernel(
+    const VIN *__restrict__ v, typename Ar<R>::GT *__restrict__ gbar, int ldg, int N, int B,
+    const typename Ar<R>::TW *__restrict__ tw)
+{
+    using D = D16<LOG2H>;
+    using F = Fa<R>;
+    using T_ = typename F::T;
+    constexpr int E = D::E, T = D::T, H = D::H, L = D::L;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int grp = threadIdx.x / T, t = threadIdx.x % T;
+    CxT<R> *buf = reinterpret_cast<CxT<R> *>(smem_raw) + grp * gslots<R, LOG2H>();
+    const int f = min(blockIdx.x * D::FPB + grp, B - 1);
+    const bool live = blockIdx.x * D::FPB + grp < B;
+    const VIN *vf = v + (size_t)f * N;
+    // (-1)^n (2n+1) v_n / M staged in the exchange buffer (N <= L values of the
+    // arithmetic type fit in its 2L words)
+    T_ *ws = reinterpret_cast<T_ *>(buf);
+    for (int n = t; n < N; n += T) {
+        const T_ x = F::mul(F::of_int(2 * n + 1), F::pow2(in_of<R>(vf[n]), -(LOG2H + 2)));
+        ws[n] = (n & 1) ? F::neg(x) : x;
+    }
+    fsync<T>();
+    // zbar_i: i < H holds n = 2i, i >= H holds n = 2(L - 1 - i) + 1
+    auto zbar = [&](int i) -> T_ {
+        const int n = (i < H) ? 2 * i : 2 * (L - 1 - i) + 1;
+        return n < N ? ws[n] : F::zero();
+    };
+    CxT<R> x[E];
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+        const int m = t + b * T;
+        x[b] = {zbar(2 * m), F::neg(zbar(2 * m + 1))};
+    }
+    fsync<T>();   // the staged values are read before the first pass writes buf
+    fft16<R, LOG2H>(x, buf, t, tw);
+    fsync<T>();
+    if (!live) return;
+    typename Ar<R>::GT *gf = gbar + (size_t)f * ldg;
+#pragma unroll
+    for (int b = 0; b < E; ++b) {
+        const int k = t + b * T;
+        const CxT<R> pk = buf[D::pc(k)], pm = buf[D::pc((H - k) & (H - 1))];
+        // Ybar_k = conj(pk), Ybar_{H-k} = conj(pm)
+        const T_ yr = pk.re, yi = F::neg(pk.im), mr = pm.re, mi = F::neg(pm.im);
+        if (k == 0) {
+            gf[L] = Ar<R>::to_g(F::norm(F::pow2(F::add(yr, yi), 1)));
+            gf[H] = Ar<R>::to_g(F::norm(F::pow2(F::sub(yr, yi), 1)));
+            gf[0] = Ar<R>::to_g(F::zero());
+            continue;
+        }
+        T_ ec, es;
+        twid(tw, 2 * k, ec, es);   // e_k = e^{2 pi i k / L}
+        const T_ one = F::of_int(1);
+        const T_ am = F::sub(one, es), ap = F::add(one, es);
+        // Wbar_k = ((1 - es) - i ec) Ybar_k + ((1 + es) + i ec) conj(Ybar_{H-k})
+        const T_ wr = F::add(F::add(F::mul(am, yr), F::mul(ec, yi)), F::add(F::mul(ap, mr), F::mul(ec, mi)));
+        const T_ wi = F::add(F::sub(F::mul(am, yi), F::mul(ec, yr)), F::sub(F::mul(ec, mr), F::mul(ap, mi)));
+        T_ c, sn;
+        twid(tw, k, c, sn);        // e^{2 pi i k / M}
+        const T_ gk = F::sub(F::mul(F::sub(one, c), wr), F::mul(sn, wi));
+        const T_ gl = F::add(F::mul(F::add(one, c), wr), F::mul(sn, wi));
+        gf[k] = Ar<R>::to_g(F::norm(gk));
+        gf[L - k] = Ar<R>::to_g(F::norm(gl));
+    }
+}
+
+template <class R, class VIN, int LOG2H>
+int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+{
+    using D = D16<LOG2H>;
+    auto kern = dst16_adjoint_kernel<R, VIN, LOG2H>;
+    const size_t smem = d16_smem<R, LOG2H>();
+    LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int grid = (B + D::FPB - 1) / D::FPB;
+    kern<<<grid, D::THREADS, smem, st>>>(static_cast<const VIN *>(v), static_cast<typename Ar<R>::GT *>(gbar), ldg,
+                                         N, B, static_cast<const typename Ar<R>::TW *>(tw));
+    LEG_LAUNCH_CHECK("dst16_adjoint_kernel");
+    return LEG_OK;
+}
+
+template <class R, class VIN, int LO, int HI>
+int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+{
+    if constexpr (LO > HI) {
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
+    } else {
+        if (lg == LO) return launch_adj<R, VIN, LO>(v, gbar, ldg, N, B, tw, st);
+        return dispatch_adj<R, VIN, LO + 1, HI>(lg, v, gbar, ldg, N, B, tw, st);
+    }
+}
+
 template <class R, int LOG2H, int XE>
 int launch_fwd(const void *G, int ldg, void *c, int N, int B, const void *tw, cudaStream_t st, const int *rowfn,
                const long long *out_off, const int *n_out)
@@ -179,4 +287,13 @@ int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, v
     default:
         return dispatch_fwd<float, 6, 13>(log2h, log2e, G, ldg, c, N, B, tw, st, rowfn, out_off, n_out);
     }
+}
+
+// The adjoint of leg_dst16_forward (radix-8 passes): v (B x N: FP32 for
+// LEG_SPLIT_FP16, FP64 for LEG_F64) to gbar (B x ldg, rows 0..L written).
+int leg_dst16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
+                      cudaStream_t st)
+{
+    if (dtype == LEG_F64) return dispatch_adj<double, double, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
+    return dispatch_adj<dfl, float, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
 }

@@ -608,6 +608,8 @@ int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B
     const int lg = ilog2(p->L);
     switch (p->dtype) {
     case LEG_F64:
+        if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
+            return leg_dst16_adjoint(LEG_F64, lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
         if (p->fft_variant != LEG_TRANSFORM_STOCKHAM && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_adjoint(LEG_F64, lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
         return dispatch_dct_adjoint<double, double, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->tw64, st);
@@ -615,6 +617,8 @@ int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B
     case LEG_BF16:
         return dispatch_adjoint<float, float, 2, 14>(lg, v, gbar, ldg, p->N, B, p->tw32, st);
     case LEG_SPLIT_FP16:
+        if (p->fft_variant == LEG_TRANSFORM_SINE && lg - 1 >= DCT16_MIN_LOG2H)
+            return leg_dst16_adjoint(LEG_SPLIT_FP16, lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
         if (p->fft_variant != LEG_TRANSFORM_STOCKHAM && lg - 1 >= DCT16_MIN_LOG2H)
             return leg_dct16_adjoint(LEG_SPLIT_FP16, lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);
         return dispatch_dct_adjoint<dfl, float, 1, 13>(lg - 1, v, gbar, ldg, p->N, B, p->twdf, st);

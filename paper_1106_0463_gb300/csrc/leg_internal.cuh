@@ -279,6 +279,8 @@ int leg_dct16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, 
 // LEG_SPLIT_FP16 (double-float G, FP32 c) or LEG_F32 / LEG_BF16 (FP32)
 int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, void *c, int N, int B,
                       const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
+int leg_dst16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
+                      cudaStream_t st);
 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,

@@ -203,3 +203,64 @@ def test_sine_form_argument_checks(leg):
         p.set_transform(7)
     with pytest.raises(leg.LegError):
         p.set_transform(leg.TRANSFORM_REG, 32)
+
+
+# ---------------------------------------------------------------- the adjoint
+@pytest.mark.parametrize("dtype_name,tol", [("F64", 1e-11), ("SPLIT_FP16", 1e-6)])
+def test_sine_form_adjoint_is_the_transpose(leg, oracle, dtype_name, tol):
+    # leg_backward on a sine-form plan against the explicit L = R A of the
+    # oracle's route 2 on the same grid
+    N, M, K, Q, B = 64, 256, 65, 17, 5
+    plan = leg.Plan(N, M, K, Q, getattr(leg, dtype_name), flags=leg.FLAG_SINE_FORM)
+    L = oracle.twisted_dft_matrix(N, M) @ oracle.abel_operator(M, K, Q, True)
+    v = np.random.default_rng(3).standard_normal((B, N))
+    if dtype_name != "F64":
+        v = v.astype(np.float32).astype(np.float64)
+    dt = torch.float64 if dtype_name == "F64" else torch.float32
+    df = plan.backward(torch.tensor(v, dtype=dt, device="cuda")).double().cpu().numpy()
+    plan.status()
+    assert relerr(df, v @ L) < tol
+
+
+@pytest.mark.parametrize("M", [256, 2048, 8192, 32768])
+def test_sine_form_adjoint_at_every_length(leg, oracle, M):
+    # FP64: both transform kernels' backward passes against the oracle's
+    # route 1 transposed (the configuration is exact, M > N + K - 1).  The
+    # (2n+1) weights, up to 2N = M/2, carry the kernels' rounding into the
+    # result, so the bound grows with M (8e-15 M; measured at M = 32768: the
+    # real-even adjoint 1.1e-10, the sine form 2.1e-11).  Split FP16: the two
+    # kernels agree to the split GEMM's resolution (up to M = 8192: with K = 65
+    # and N = M/4 the transposed GEMM sums rows whose result cancels to a
+    # degree-64 polynomial, and its relative error grows with N/K)
+    N, K, B = M // 4, 65, 6
+    g = torch.Generator(device="cpu").manual_seed(M)
+    v = torch.randn(B, N, generator=g, dtype=torch.float64)
+    ref = oracle.adjoint_direct((K + N) // 2 + 4, K, v.numpy())
+    plan = leg.Plan(N, M, K, 0, leg.F64)
+    for tr in (leg.TRANSFORM_REG, leg.TRANSFORM_SINE):
+        plan.set_transform(tr)
+        d = plan.backward(v.cuda()).cpu().numpy()
+        plan.status()
+        assert relerr(d, ref) < 8e-15 * M, (tr, relerr(d, ref))
+    if M <= 8192:
+        plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+        v32 = v.float().cuda()
+        plan.set_transform(leg.TRANSFORM_REG)
+        d_reg = plan.backward(v32).double().cpu().numpy()
+        plan.set_transform(leg.TRANSFORM_SINE)
+        d_sine = plan.backward(v32).double().cpu().numpy()
+        plan.status()
+        scale = np.max(np.abs(d_reg), axis=1, keepdims=True)
+        assert np.max(np.abs(d_sine - d_reg) / scale) < 1e-7
+
+
+def test_sine_form_dot_product_identity_f64(leg):
+    # <L f, v> = <f, L^T v> with the sine-form forward and its adjoint
+    N, M, K, B = 1024, 4096, 513, 4
+    plan = leg.Plan(N, M, K, 0, leg.F64, flags=leg.FLAG_SINE_FORM)
+    g = torch.Generator(device="cpu").manual_seed(9)
+    f = torch.randn(B, K, dtype=torch.float64, generator=g).cuda()
+    v = torch.randn(B, N, dtype=torch.float64, generator=g).cuda()
+    lhs = (plan.forward(f) * v).sum(1)
+    rhs = (f * plan.backward(v)).sum(1)
+    assert torch.allclose(lhs, rhs, rtol=1e-11, atol=1e-11 * float(lhs.abs().max()))
