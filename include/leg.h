@@ -196,7 +196,10 @@ LEG_API int leg_forward_profiled(leg_plan_t plan, const void *f, void *c, int B,
 /*
  * leg_backward -- df = L^T dc, the exact adjoint (transpose) of the linear
  * map of leg_forward for the same plan: the transposed twist + Fourier sum
- * followed by the transposed Abel operator.
+ * followed by the transposed Abel operator.  The transposed transform follows
+ * the plan's transform kernel: the transpose of the sine-form pipeline
+ * (Eq. 2.13) on plans that use it, of the real-even one (Eq. 2.4, 2.5)
+ * otherwise; both are the transpose of the same map.
  *   dc device, B x N (FP64 for LEG_F64, FP32 otherwise).
  *   df device, B x K (same type); overwritten.
  */
