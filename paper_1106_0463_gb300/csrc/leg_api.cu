@@ -515,6 +515,10 @@ extern "C" int leg_backward(leg_plan_t p, const void *dc, void *df, int B, cudaS
             return leg_set_error(LEG_ERR_UNSUPPORTED, "leg_backward is not available for LEG_BF16");
         }
     }
+    if (leg_fft_adjoint_writes_planes(p)) {
+        if ((rc = leg_fft_adjoint_planes(p, dc, B, st))) return rc;
+        return leg_gemm_split_adj_planes(p, df, B, st);
+    }
     if ((rc = leg_fft_adjoint(p, dc, p->Gbar, p->ldg, B, st))) return rc;
     switch (p->dtype) {
     case LEG_F64:

@@ -29,6 +29,7 @@
 // and there is no recombination after the FFT and no prefix scan, so the
 // outputs need no first difference of two large sums.
 #include "leg_rtile.cuh"
+#include "leg_split.cuh"
 
 namespace {
 
@@ -133,10 +134,16 @@ __global__ void __launch_bounds__(D16<LOG2H, XE>::THREADS, fwd_minb<R, LOG2H, XE
 //   enter the sine form: phi vanishes at y = 0).
 // Every gbar index receives exactly one of these terms, so each thread writes
 // its own outputs.
-template <class R, class VIN, int LOG2H>
+// With PLANES (double-float only) the kernel writes, instead of gbar, the
+// seven FP16 planes of gbar and its per-function scale (the input of the
+// split-FP16 transposed GEMM: sp, rows of npr columns, zero beyond L): the row
+// is staged in shared memory after the transform, its maximum reduced over the
+// function's threads, and the planes written 8 columns per 16-byte store, the
+// same values the separate split of gbar would write.
+template <class R, class VIN, int LOG2H, bool PLANES>
 __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dst16_adjoint_kernel(
     const VIN *__restrict__ v, typename Ar<R>::GT *__restrict__ gbar, int ldg, int N, int B,
-    const typename Ar<R>::TW *__restrict__ tw)
+    const typename Ar<R>::TW *__restrict__ tw, LegSplitIn sp, int npr)
 {
     using D = D16<LOG2H>;
     using F = Fa<R>;
@@ -170,8 +177,10 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dst16_a
     fsync<T>();   // the staged values are read before the first pass writes buf
     fft16<R, LOG2H>(x, buf, t, tw);
     fsync<T>();
-    if (!live) return;
-    typename Ar<R>::GT *gf = gbar + (size_t)f * ldg;
+    if (!PLANES && !live) return;
+    // gbar_{ia[b]} = ga[b], gbar_{ib[b]} = gb[b] (k = t + b T: ia = k, ib = L - k;
+    // k = 0: ia = L, ib = H; gbar_0 = 0 besides)
+    T_ ga[E], gb[E];
 #pragma unroll
     for (int b = 0; b < E; ++b) {
         const int k = t + b * T;
@@ -179,9 +188,8 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dst16_a
         // Ybar_k = conj(pk), Ybar_{H-k} = conj(pm)
         const T_ yr = pk.re, yi = F::neg(pk.im), mr = pm.re, mi = F::neg(pm.im);
         if (k == 0) {
-            gf[L] = Ar<R>::to_g(F::norm(F::pow2(F::add(yr, yi), 1)));
-            gf[H] = Ar<R>::to_g(F::norm(F::pow2(F::sub(yr, yi), 1)));
-            gf[0] = Ar<R>::to_g(F::zero());
+            ga[b] = F::norm(F::pow2(F::add(yr, yi), 1));
+            gb[b] = F::norm(F::pow2(F::sub(yr, yi), 1));
             continue;
         }
         T_ ec, es;
@@ -193,35 +201,82 @@ __global__ void __launch_bounds__(D16<LOG2H>::THREADS, D16<LOG2H>::MINB) dst16_a
         const T_ wi = F::add(F::sub(F::mul(am, yi), F::mul(ec, yr)), F::sub(F::mul(ec, mr), F::mul(ap, mi)));
         T_ c, sn;
         twid(tw, k, c, sn);        // e^{2 pi i k / M}
-        const T_ gk = F::sub(F::mul(F::sub(one, c), wr), F::mul(sn, wi));
-        const T_ gl = F::add(F::mul(F::add(one, c), wr), F::mul(sn, wi));
-        gf[k] = Ar<R>::to_g(F::norm(gk));
-        gf[L - k] = Ar<R>::to_g(F::norm(gl));
+        ga[b] = F::norm(F::sub(F::mul(F::sub(one, c), wr), F::mul(sn, wi)));
+        gb[b] = F::norm(F::add(F::mul(F::add(one, c), wr), F::mul(sn, wi)));
+    }
+    if constexpr (!PLANES) {
+        typename Ar<R>::GT *gf = gbar + (size_t)f * ldg;
+#pragma unroll
+        for (int b = 0; b < E; ++b) {
+            const int k = t + b * T;
+            gf[k == 0 ? L : k] = Ar<R>::to_g(ga[b]);
+            gf[k == 0 ? H : L - k] = Ar<R>::to_g(gb[b]);
+        }
+        if (t == 0) gf[0] = Ar<R>::to_g(F::zero());
+    } else {
+        static_assert(std::is_same<R, dfl>::value, "planes are written from double-float values");
+        fsync<T>();   // every value of buf has been read
+        float2 *gs = reinterpret_cast<float2 *>(buf);   // npr <= L + 32 values fit in the buffer
+        float m = 0.0f;
+#pragma unroll
+        for (int b = 0; b < E; ++b) {
+            const int k = t + b * T;
+            gs[k == 0 ? L : k] = make_float2(ga[b].hi, ga[b].lo);
+            gs[k == 0 ? H : L - k] = make_float2(gb[b].hi, gb[b].lo);
+            m = fmaxf(m, fmaxf(fabsf(ga[b].hi), fabsf(gb[b].hi)));
+        }
+        if (t == 0) gs[0] = make_float2(0.0f, 0.0f);
+        for (int j = L + 1 + t; j < npr; j += T) gs[j] = make_float2(0.0f, 0.0f);
+        // the row maximum over the function's threads
+        float *red = reinterpret_cast<float *>(reinterpret_cast<T_ *>(reinterpret_cast<CxT<R> *>(smem_raw) +
+                                                                      D::FPB * gslots<R, LOG2H>()) +
+                                               grp * D::WARPS);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if ((t & 31) == 0) red[t >> 5] = m;
+        fsync<T>();
+        float mm = 0.0f;
+        for (int w = 0; w < D::WARPS; ++w) mm = fmaxf(mm, red[w]);
+        const int e = split_scale_exp(mm);
+        if (!live) return;
+        if (t == 0) sp.fexp[f] = e;
+        const float SC = __int_as_float((127 + sp.fbits) << 23), ISC = __int_as_float((127 - sp.fbits) << 23);
+        __half *P = sp.base + (size_t)f * sp.ld;
+        for (int c8 = t; c8 < npr / 8; c8 += T) {
+            float2 v8[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v8[i] = gs[8 * c8 + i];
+            split_planes8<float2>(v8, e, SC, ISC, P + 8 * c8, sp.pstride);
+        }
     }
 }
 
-template <class R, class VIN, int LOG2H>
-int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+template <class R, class VIN, int LOG2H, bool PLANES>
+int launch_adj(const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st,
+               const LegSplitIn &sp, int npr)
 {
     using D = D16<LOG2H>;
-    auto kern = dst16_adjoint_kernel<R, VIN, LOG2H>;
+    if (PLANES && (size_t)npr * sizeof(float2) > (size_t)gslots<R, LOG2H>() * sizeof(CxT<R>))
+        return leg_set_error(LEG_ERR_UNSUPPORTED, "adjoint planes exceed the exchange buffer");
+    auto kern = dst16_adjoint_kernel<R, VIN, LOG2H, PLANES>;
     const size_t smem = d16_smem<R, LOG2H>();
     LEG_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int grid = (B + D::FPB - 1) / D::FPB;
     kern<<<grid, D::THREADS, smem, st>>>(static_cast<const VIN *>(v), static_cast<typename Ar<R>::GT *>(gbar), ldg,
-                                         N, B, static_cast<const typename Ar<R>::TW *>(tw));
+                                         N, B, static_cast<const typename Ar<R>::TW *>(tw), sp, npr);
     LEG_LAUNCH_CHECK("dst16_adjoint_kernel");
     return LEG_OK;
 }
 
-template <class R, class VIN, int LO, int HI>
-int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st)
+template <class R, class VIN, bool PLANES, int LO, int HI>
+int dispatch_adj(int lg, const void *v, void *gbar, int ldg, int N, int B, const void *tw, cudaStream_t st,
+                 const LegSplitIn &sp, int npr)
 {
     if constexpr (LO > HI) {
         return leg_set_error(LEG_ERR_UNSUPPORTED, "transform length out of range");
     } else {
-        if (lg == LO) return launch_adj<R, VIN, LO>(v, gbar, ldg, N, B, tw, st);
-        return dispatch_adj<R, VIN, LO + 1, HI>(lg, v, gbar, ldg, N, B, tw, st);
+        if (lg == LO) return launch_adj<R, VIN, LO, PLANES>(v, gbar, ldg, N, B, tw, st, sp, npr);
+        return dispatch_adj<R, VIN, PLANES, LO + 1, HI>(lg, v, gbar, ldg, N, B, tw, st, sp, npr);
     }
 }
 
@@ -294,6 +349,16 @@ int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, v
 int leg_dst16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
                       cudaStream_t st)
 {
-    if (dtype == LEG_F64) return dispatch_adj<double, double, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
-    return dispatch_adj<dfl, float, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st);
+    const LegSplitIn none = {};
+    if (dtype == LEG_F64)
+        return dispatch_adj<double, double, false, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st, none, 0);
+    return dispatch_adj<dfl, float, false, 6, 13>(log2h, v, gbar, ldg, N, B, tw, st, none, 0);
+}
+
+// The split-FP16 adjoint straight into the transposed GEMM's input: the
+// planes and scales of sp (B rows of npr columns) instead of gbar.
+int leg_dst16_adjoint_planes(int log2h, const float *v, const LegSplitIn &sp, int npr, int N, int B,
+                             const void *twdf, cudaStream_t st)
+{
+    return dispatch_adj<dfl, float, true, 6, 13>(log2h, v, nullptr, 0, N, B, twdf, st, sp, npr);
 }

@@ -602,6 +602,18 @@ int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, c
     return leg_set_error(LEG_ERR_INVALID_ARG, "bad dtype");
 }
 
+bool leg_fft_adjoint_writes_planes(const leg_plan *p)
+{
+    return p->dtype == LEG_SPLIT_FP16 && p->fft_variant == LEG_TRANSFORM_SINE && ilog2(p->L) - 1 >= DCT16_MIN_LOG2H;
+}
+
+int leg_fft_adjoint_planes(const leg_plan *p, const void *v, int B, cudaStream_t st)
+{
+    if (B == 0) return LEG_OK;
+    return leg_dst16_adjoint_planes(ilog2(p->L) - 1, static_cast<const float *>(v), leg_split_workspace(p),
+                                    leg_adj_depth(p), p->N, B, p->twdf, st);
+}
+
 int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B, cudaStream_t st)
 {
     if (B == 0) return LEG_OK;

@@ -254,6 +254,10 @@ int leg_gemm_f32_adj(const float *Gb, int ldg, const float *A, int lda, float *D
 // gkind: 0 = double G, 1 = float G, 2 = double-float G (float2)
 int leg_fft_forward(const leg_plan *p, const void *G, int ldg, void *c, int B, cudaStream_t st);
 int leg_fft_adjoint(const leg_plan *p, const void *v, void *gbar, int ldg, int B, cudaStream_t st);
+// split-FP16 plans on the sine-form transform: the adjoint transform writes the
+// transposed GEMM's input planes directly (no gbar, no separate split)
+bool leg_fft_adjoint_writes_planes(const leg_plan *p);
+int leg_fft_adjoint_planes(const leg_plan *p, const void *v, int B, cudaStream_t st);
 int leg_fft_forward_f64(const leg_plan *p, const double *G, int ldg, double *c, int B, cudaStream_t st);
 
 // Forward transform kernels of a plan (leg_plan::fft_variant).  All compute the
@@ -281,6 +285,8 @@ int leg_dst16_forward(int dtype, int log2h, int log2e, const void *G, int ldg, v
                       const void *tw, cudaStream_t st, const int *rowfn, const long long *out_off, const int *n_out);
 int leg_dst16_adjoint(int dtype, int log2h, const void *v, void *gbar, int ldg, int N, int B, const void *tw,
                       cudaStream_t st);
+int leg_dst16_adjoint_planes(int log2h, const float *v, const LegSplitIn &sp, int npr, int N, int B,
+                             const void *twdf, cudaStream_t st);
 
 // plain method (leg_plain.cu): g_j from a closed form at the quadrature points
 int leg_plain_g(const leg_plan *p, int family, const double *params, int B, double *G, int ldg,
@@ -294,6 +300,8 @@ int leg_gemm_split_fwd(leg_plan *p, int B, cudaStream_t st);
 int leg_gemm_bf16_fwd(leg_plan *p, int B, void *out, int ldo, cudaStream_t st);   // rows p->grows
 int leg_bf16_prepare_input(const leg_plan *p, const float *f, int B, cudaStream_t st);
 int leg_gemm_split_adj(leg_plan *p, void *df, int B, cudaStream_t st);
+// the transposed GEMM from planes already in the plan's split workspace
+int leg_gemm_split_adj_planes(leg_plan *p, void *df, int B, cudaStream_t st);
 int leg_build_split_transposed(leg_plan *p);
 // collapsed plans (LEG_FLAG_COLLAPSED): c = L f and df = L^T dc, FP32
 int leg_gemm_split_collapsed_fwd(leg_plan *p, int B, float *c, cudaStream_t st);
