@@ -686,7 +686,7 @@ def ragged(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=
     return out
 
 
-def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3):
+def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20, warmup=3, transform=None):
     """B=1024, K=4097, N=2048, M=8192: forward + backward of the split path
     (leg_forward, leg_backward) against the FP64 GPU path, errors of both
     directions against the oracle (route 1 and route 1 transposed)."""
@@ -702,7 +702,11 @@ def differentiation(leg, torch, flush, rank, peaks, peak_src, with_ref, steps=20
     v = torch.from_numpy(v_np).cuda()
     df = torch.empty_like(x)
     split.reserve(B)
-    tuned = split.autotune(x)   # the forward's GEMM tile width and transform kernel, timed on this batch
+    if transform is None:
+        tuned = split.autotune(x)   # the forward's GEMM tile width and transform kernel, timed on this batch
+    else:                           # fixed from the command line
+        split.set_transform(transform)
+        tuned = {"tn": 0, "fft": split.transform}
 
     def fwd_bwd():
         split.forward(x, c)
@@ -791,7 +795,11 @@ def ragged_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
 def differentiation_line(args, leg, torch, dist, flush, rank, world, peaks, peak_src):
     """--workload diff_b1024_k4097: forward + backward (leg_forward, leg_backward)
     at B=1024, K=4097, N=2048, M=8192 as the timed workload."""
-    r = differentiation(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup)
+    fixed = None
+    if args.transform is not None:
+        fixed = {"reg": leg.TRANSFORM_REG, "stockham": leg.TRANSFORM_STOCKHAM, "sine": leg.TRANSFORM_SINE}[args.transform]
+    r = differentiation(leg, torch, flush, rank, peaks, peak_src, rank == 0, steps=args.steps, warmup=args.warmup,
+                        transform=fixed)
     ms = max_over_ranks(torch, dist, r["ms_per_step"], "cuda")
     if rank == 0:
         line = {"metric": METRIC + " (forward + backward)", "value": whole_job_rate(world, 1024 * 2048, ms),
