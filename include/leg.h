@@ -457,9 +457,37 @@ LEG_API int leg_forward_noalloc(leg_plan_t plan, const float *f, float *c, int B
  * lets the copies run at full speed and overlap; pageable memory works but
  * the copies then run through a staging buffer.  The plan keeps device
  * copies of the largest batch it has seen (B x (K + N) values) and two
- * internal streams; growing them synchronises the device.
+ * internal streams; growing them synchronises the device.  For a stream of
+ * batches, leg_plan_set_host_overlap lets each call's input copy run during
+ * the previous call's kernels.
  */
 LEG_API int leg_forward_host(leg_plan_t plan, const void *f_host, void *c_host, int B, cudaStream_t stream);
+
+/*
+ * leg_plan_set_host_overlap -- how leg_forward_host orders its input copy for
+ * a stream of batches.  (A library convenience with no counterpart in the
+ * paper.)
+ *   on = 0 (default): every step of leg_forward_host is ordered after the
+ *      work already queued on `stream`.
+ *   on = 1: for LEG_SPLIT_FP16 and LEG_BF16 plans with page-locked, mapped
+ *      host buffers, leg_forward_host copies f_host with a copy engine into
+ *      one of two device staging buffers of the plan (the calls alternate
+ *      between them) on an internal stream, and that copy waits only for the
+ *      previous call that used the same staging buffer to finish, not for the
+ *      rest of the work on `stream`: the input of one call crosses the host
+ *      link while the kernels of the call before it run.  f_host must
+ *      therefore hold the batch when the call is made (written by the host,
+ *      or by device work the caller has already synchronised).  The kernels
+ *      read the staging buffer; c_host is written in place by the last kernel
+ *      as with on = 0 and is complete once `stream` has reached the end of
+ *      the call.  Calls made while `stream` is being captured, and other
+ *      plans and buffers, run as with on = 0.
+ * Results equal leg_forward's bit for bit either way.  The staging buffers
+ * (2 x B x K FP32 values of the largest batch seen) are allocated by the
+ * first call that needs them; growing them synchronises the device.
+ * Errors: LEG_ERR_INVALID_ARG for a NULL plan or on outside {0, 1}.
+ */
+LEG_API int leg_plan_set_host_overlap(leg_plan_t plan, int on);
 
 /*
  * leg_memory_info -- device memory the library holds at this moment for the

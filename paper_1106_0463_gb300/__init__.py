@@ -81,6 +81,7 @@ def _load():
         "leg_plan_status": ([vp, i], i),
         "leg_plan_set_wait_limit": ([vp, ctypes.c_longlong], i),
         "leg_plan_set_tile": ([vp, i], i),
+        "leg_plan_set_host_overlap": ([vp, i], i),
         "leg_plan_set_transform": ([vp, i, i], i),
         "leg_plan_get_transform": ([vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, ctypes.POINTER(i), ctypes.POINTER(i)], i),
@@ -220,6 +221,13 @@ class Plan:
     def set_tile(self, tn: int):
         """Functions per CTA-pair tile of the tensor-core GEMM (0 = automatic)."""
         _check(_lib.leg_plan_set_tile(self._h, int(tn)))
+
+    def set_host_overlap(self, on: bool):
+        """leg_plan_set_host_overlap: with on, forward_host on pinned buffers
+        copies each batch's input with a copy engine ordered only after the
+        previous use of its staging buffer, so that it overlaps the previous
+        call's kernels; f_host must hold the batch when the call is made."""
+        _check(_lib.leg_plan_set_host_overlap(self._h, 1 if on else 0))
 
     def set_transform(self, variant: int, radix: int = 0):
         """Kernel of the forward transform stage: TRANSFORM_REG, TRANSFORM_STOCKHAM

@@ -32,7 +32,8 @@ void free_plan(leg_plan *p)
 {
     if (!p) return;
     leg_ragged_forget_plan(p);
-    if (p->fwd_exec) cudaGraphExecDestroy(p->fwd_exec);
+    for (auto &e : p->fwd)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
     if (p->cap) cudaStreamDestroy(p->cap);
     leg_host_free(p);
     free_workspace(p);
@@ -414,9 +415,9 @@ int forward_impl(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, c
 }  // namespace
 
 // Launches of the same call replayed from a CUDA graph: the first call with a
-// key runs directly, the second captures and instantiates, later ones replay.
-// A call made while the caller's stream is itself being captured runs
-// directly (its launches join the caller's graph).
+// key runs directly, the second captures and instantiates, later ones replay
+// (two keys cached).  A call made while the caller's stream is itself being
+// captured runs directly (its launches join the caller's graph).
 extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st)
 {
     int rc = check_plan(p);
@@ -437,20 +438,27 @@ extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStre
     key.fft = p->fft_variant;
     key.fft_log2e = p->fft_log2e;
     key.wait = p->wait_limit;
-    if (p->fwd_exec && key == p->fwd_key) {
-        LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
+    leg_plan::GraphEntry *e = nullptr;
+    for (auto &x : p->fwd)
+        if (x.seen && x.key == key) e = &x;
+    if (e && e->exec) {
+        e->used = ++p->fwd_clock;
+        LEG_CUDA_TRY(cudaGraphLaunch(e->exec, st));
         return LEG_OK;
     }
-    if (p->fwd_exec) {
-        cudaGraphExecDestroy(p->fwd_exec);
-        p->fwd_exec = nullptr;
-    }
-    if (!(p->fwd_seen && key == p->fwd_key)) {
-        p->fwd_key = key;
-        p->fwd_seen = true;
+    if (!e) {   // a new key replaces the least recently used entry
+        e = &p->fwd[0];
+        for (auto &x : p->fwd)
+            if (x.used < e->used) e = &x;
+        if (e->exec) cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+        e->key = key;
+        e->seen = true;
+        e->used = ++p->fwd_clock;
         return forward_impl(p, f, c, B, st, nullptr);
     }
     // second call with this key: capture the launches on the plan's own stream
+    e->used = ++p->fwd_clock;
     if (!p->cap) LEG_CUDA_TRY(cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking));
     LEG_CUDA_TRY(cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal));
     rc = forward_impl(p, f, c, B, p->cap, nullptr);
@@ -459,19 +467,19 @@ extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStre
     if (rc || ec != cudaSuccess || !g) {
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
-        p->fwd_seen = false;
+        e->seen = false;
         if (rc) return rc;
         return forward_impl(p, f, c, B, st, nullptr);   // capture unavailable: run directly
     }
-    const cudaError_t ei = cudaGraphInstantiateWithFlags(&p->fwd_exec, g, 0);
+    const cudaError_t ei = cudaGraphInstantiateWithFlags(&e->exec, g, 0);
     cudaGraphDestroy(g);
     if (ei != cudaSuccess) {
         cudaGetLastError();
-        p->fwd_exec = nullptr;
-        p->fwd_seen = false;
+        e->exec = nullptr;
+        e->seen = false;
         return forward_impl(p, f, c, B, st, nullptr);
     }
-    LEG_CUDA_TRY(cudaGraphLaunch(p->fwd_exec, st));
+    LEG_CUDA_TRY(cudaGraphLaunch(e->exec, st));
     return LEG_OK;
 }
 
@@ -608,6 +616,14 @@ extern "C" int leg_plan_set_tile(leg_plan_t p, int tn)
         return leg_set_error(LEG_ERR_INVALID_ARG, "tile width must be 0 or a multiple of 16 in 16.." +
                                                       std::to_string(maxtn) + " for this plan");
     p->tn = tn;
+    return LEG_OK;
+}
+
+extern "C" int leg_plan_set_host_overlap(leg_plan_t p, int on)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (on != 0 && on != 1) return leg_set_error(LEG_ERR_INVALID_ARG, "on must be 0 or 1");
+    p->host_overlap = on;
     return LEG_OK;
 }
 

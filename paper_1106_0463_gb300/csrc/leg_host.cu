@@ -1,12 +1,15 @@
 // leg_forward_host: leg_forward on host buffers.  Page-locked host buffers
 // mapped into the device's address space are used in place by the split-FP16
 // and BF16 paths (their first kernel reads each input value once, their last
-// writes each coefficient once).  Otherwise the batch is copied to the
-// device, transformed and copied back with the copies overlapped with the
-// computation: for the split-FP16 path the host-to-device copy runs in
-// LEG_HOST_CHUNKS pieces on an internal stream and the input split of each
-// piece starts as soon as it has landed; the transform runs per piece and
-// each piece's coefficients are copied back while the next piece is
+// writes each coefficient once).  With the plan's host overlap on, the input
+// of such a call is instead copied by a copy engine into one of two staging
+// buffers, ordered only after the last use of that buffer, so that it crosses
+// the host link while the previous call's kernels run.  Otherwise the batch
+// is copied to the device, transformed and copied back with the copies
+// overlapped with the computation: for the split-FP16 path the host-to-device
+// copy runs in LEG_HOST_CHUNKS pieces on an internal stream and the input
+// split of each piece starts as soon as it has landed; the transform runs per
+// piece and each piece's coefficients are copied back while the next piece is
 // transformed.  The Abel GEMM (or the collapsed GEMM) runs once on the whole
 // batch in between.  Results are the same as leg_forward's bit for bit: every
 // kernel computes each function independently of the others.
@@ -20,6 +23,13 @@ struct LegHostState {
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t start = nullptr, done = nullptr;
     cudaEvent_t in[LEG_HOST_CHUNKS] = {}, out[LEG_HOST_CHUNKS] = {};
+    // host overlap: two staging buffers of the input, the event after the
+    // last call that read each (recorded on that call's stream) and the
+    // event after each one's copy
+    void *stage[2] = {};
+    int stage_cap = 0;   // functions each holds
+    int slot = 0;        // the buffer the next call uses
+    cudaEvent_t stage_free[2] = {}, stage_ready[2] = {};
 };
 
 void leg_host_free(leg_plan *p)
@@ -32,6 +42,11 @@ void leg_host_free(leg_plan *p)
         if (h->in[i]) cudaEventDestroy(h->in[i]);
         if (h->out[i]) cudaEventDestroy(h->out[i]);
     }
+    for (int i = 0; i < 2; ++i) {
+        leg_dev_free(h->stage[i]);
+        if (h->stage_free[i]) cudaEventDestroy(h->stage_free[i]);
+        if (h->stage_ready[i]) cudaEventDestroy(h->stage_ready[i]);
+    }
     if (h->start) cudaEventDestroy(h->start);
     if (h->done) cudaEventDestroy(h->done);
     if (h->h2d) cudaStreamDestroy(h->h2d);
@@ -42,7 +57,8 @@ void leg_host_free(leg_plan *p)
 
 namespace {
 
-int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
+// The plan's copy state: streams and events, created by the first call.
+int host_base(leg_plan *p, LegHostState **out)
 {
     if (!p->host) {
         LegHostState *h = new (std::nothrow) LegHostState();
@@ -56,8 +72,21 @@ int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
             LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->in[i], cudaEventDisableTiming));
             LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->out[i], cudaEventDisableTiming));
         }
+        for (int i = 0; i < 2; ++i) {
+            LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->stage_free[i], cudaEventDisableTiming));
+            LEG_CUDA_TRY(cudaEventCreateWithFlags(&h->stage_ready[i], cudaEventDisableTiming));
+        }
     }
-    LegHostState *h = p->host;
+    *out = p->host;
+    return LEG_OK;
+}
+
+// The copy state with device copies of a batch of B functions (input and output).
+int host_state(leg_plan *p, int B, size_t eb, LegHostState **out)
+{
+    LegHostState *h = nullptr;
+    int rc = host_base(p, &h);
+    if (rc) return rc;
     if (B > h->cap) {
         LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
         leg_dev_free(h->f);
@@ -92,6 +121,47 @@ const void *device_view(const void *host)
     return a.devicePointer;
 }
 
+// Host overlap: the input goes to staging buffer `slot` by a copy on the
+// internal stream that waits only for the previous call that used the same
+// buffer to finish; the kernels read it there and write c in place (cv).
+int forward_staged(leg_plan *p, const void *f_host, void *cv, int B, cudaStream_t st)
+{
+    LegHostState *h = nullptr;
+    int rc = host_base(p, &h);
+    if (rc) return rc;
+    const size_t bytes = sizeof(float) * (size_t)B * p->K;
+    if (B > h->stage_cap) {
+        LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
+        for (int i = 0; i < 2; ++i) {
+            leg_dev_free(h->stage[i]);
+            h->stage[i] = nullptr;
+        }
+        h->stage_cap = 0;
+        for (int i = 0; i < 2; ++i) {
+            const cudaError_t e = leg_dev_malloc(&h->stage[i], bytes);
+            if (e != cudaSuccess) {   // release what was taken: nothing stays half-grown
+                for (int j = 0; j < 2; ++j) {
+                    leg_dev_free(h->stage[j]);
+                    h->stage[j] = nullptr;
+                }
+                return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
+                                     std::string("leg_forward_host staging buffers: ") + cudaGetErrorString(e));
+            }
+        }
+        h->stage_cap = B;
+    }
+    const int s = h->slot;
+    // a never-recorded event counts as completed: the first use waits for nothing
+    LEG_CUDA_TRY(cudaStreamWaitEvent(h->h2d, h->stage_free[s], 0));
+    LEG_CUDA_TRY(cudaMemcpyAsync(h->stage[s], f_host, bytes, cudaMemcpyHostToDevice, h->h2d));
+    LEG_CUDA_TRY(cudaEventRecord(h->stage_ready[s], h->h2d));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(st, h->stage_ready[s], 0));
+    if ((rc = leg_forward(p, h->stage[s], cv, B, st))) return rc;
+    LEG_CUDA_TRY(cudaEventRecord(h->stage_free[s], st));
+    h->slot = s ^ 1;
+    return LEG_OK;
+}
+
 }  // namespace
 
 extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, int B, cudaStream_t st)
@@ -113,7 +183,12 @@ extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, 
     if (p->dtype == LEG_SPLIT_FP16 || p->dtype == LEG_BF16) {   // the SIMT GEMMs re-read f per tile
         const void *fv = device_view(f_host);
         void *cv = const_cast<void *>(device_view(c_host));
-        if (fv && cv) return leg_forward(p, fv, cv, B, st);
+        if (fv && cv) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+            if (p->host_overlap && cs == cudaStreamCaptureStatusNone) return forward_staged(p, f_host, cv, B, st);
+            return leg_forward(p, fv, cv, B, st);
+        }
     }
     LegHostState *h = nullptr;
     if ((rc = host_state(p, B, eb, &h))) return rc;

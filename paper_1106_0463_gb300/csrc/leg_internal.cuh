@@ -139,7 +139,10 @@ struct leg_plan {
     LegHostState *host = nullptr;   // created by the first leg_forward_host
 
     // leg_forward replays a CUDA graph of its launches when called again with
-    // the same buffers and launch parameters (the key); captured on `cap`
+    // the same buffers and launch parameters (the key); captured on `cap`.
+    // Two keys are kept (the least recently used one is replaced), so calls
+    // alternating between two buffers (leg_forward_host's staging buffers)
+    // replay too.
     struct GraphKey {
         const void *f = nullptr;
         void *c = nullptr;
@@ -153,9 +156,15 @@ struct leg_plan {
                    fft == o.fft && fft_log2e == o.fft_log2e && wait == o.wait;
         }
     };
-    GraphKey fwd_key;
-    bool fwd_seen = false;                 // the key's launches ran once directly
-    cudaGraphExec_t fwd_exec = nullptr;
+    struct GraphEntry {
+        GraphKey key;
+        bool seen = false;                 // the key's launches ran once directly
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long used = 0;       // last use (0: never)
+    };
+    GraphEntry fwd[2];
+    unsigned long long fwd_clock = 0;
+    int host_overlap = 0;                  // leg_plan_set_host_overlap
     cudaStream_t cap = nullptr;
 };
 

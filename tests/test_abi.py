@@ -68,6 +68,7 @@ def test_every_handle_entry_point_rejects_null_without_a_gpu(libpath):
         "leg_plan_status": ([vp, i], (None, 0)),
         "leg_plan_set_wait_limit": ([vp, ll], (None, 1000)),
         "leg_plan_set_tile": ([vp, i], (None, 0)),
+        "leg_plan_set_host_overlap": ([vp, i], (None, 1)),
         "leg_plan_tile_info": ([vp, i, vp, vp, vp], (None, 4, None, None, None)),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, vp, vp], (None, None, None, 4, None, None, None)),
         "leg_forward_host": ([vp, vp, vp, i, vp], (None, None, None, 4, None)),

@@ -77,3 +77,50 @@ def test_forward_host_rejects_device_tensors(leg):
     plan = leg.Plan(16, 64, 17, 0, leg.SPLIT_FP16)
     with pytest.raises(ValueError):
         plan.forward_host(torch.zeros((2, 17), device="cuda"))
+
+
+@pytest.mark.parametrize("dt", [3, 2])
+def test_host_overlap_stream_of_batches(leg, dt):
+    """With the host overlap on, each call's input copy waits only for the
+    previous user of its staging buffer: a stream of calls queued without
+    synchronising (distinct inputs and outputs, sizes that grow and shrink)
+    still gives every batch leg_forward's coefficients bit for bit, and so do
+    calls after the overlap is switched off again."""
+    N, M, K = 160, 512, 257
+    plan = leg.Plan(N, M, K, 0, dt)
+    plan.set_host_overlap(True)
+    sizes = (37, 301, 301, 5, 301, 128, 1, 301)
+    fs = [inputs(B, K, 40 + i).pin_memory() for i, B in enumerate(sizes)]
+    refs = []
+    for f in fs:
+        refs.append(plan.forward(f.cuda()).cpu())
+    torch.cuda.synchronize()
+    for rnd in range(2):
+        cs = [torch.full((f.shape[0], N), float("nan")).pin_memory() for f in fs]
+        for f, c in zip(fs, cs):
+            plan.forward_host(f, c, sync=False)
+        torch.cuda.synchronize()
+        for i, (c, ref) in enumerate(zip(cs, refs)):
+            assert torch.equal(c, ref), (rnd, i)
+    plan.set_host_overlap(False)
+    c = plan.forward_host(fs[1], torch.empty((sizes[1], N)).pin_memory())
+    assert torch.equal(c, refs[1])
+    plan.status()
+
+
+def test_host_overlap_reuses_one_input_buffer(leg):
+    """The caller refills one pinned input buffer between synchronised calls:
+    every call reads the contents it was made with."""
+    N, M, K, B = 128, 512, 257, 200
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    plan.set_host_overlap(True)
+    fh = torch.empty((B, K)).pin_memory()
+    ch = torch.empty((B, N)).pin_memory()
+    for seed in range(5):
+        f = inputs(B, K, 70 + seed)
+        ref = plan.forward(f.cuda()).cpu()
+        fh.copy_(f)
+        plan.forward_host(fh, ch)
+        assert torch.equal(ch, ref), seed
+    with pytest.raises(RuntimeError):
+        leg._check(leg._lib.leg_plan_set_host_overlap(plan._h, 2))
