@@ -176,12 +176,35 @@ LEG_API int leg_plan_info(leg_plan_t plan, int *N, int *M, int *K, int *Q, int *
  * The kernels are chained by programmatic dependent launch.  The first call
  * with given (f, c, B) and launch settings runs its launches directly, the
  * second captures them into a CUDA graph (on a stream of the plan's own) and
- * later ones replay that graph on `stream`; a change of f, c, B, the
+ * later ones replay that graph on `stream` (the graphs of the two most
+ * recently used (f, c, B, settings) keys are kept); a change of f, c, B, the
  * workspace, the tile width, the transform kernel or the wait limit starts
  * over.  A call made while `stream` is being captured by the caller launches
  * directly, so its kernels become part of the caller's graph.
  */
 LEG_API int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStream_t stream);
+
+/*
+ * leg_forward_batches -- leg_forward on nbatch batches of B functions, one
+ * after another (Theorem 1, Eq. 2.4-2.5, for each function).  (A scheduling
+ * convenience for a stream of batches; the paper has no counterpart.)
+ *   f  device, nbatch x B x K row-major (batch b starts at row b*B), the
+ *      type of leg_forward's f;
+ *   c  device, nbatch x B x N, leg_forward's c type; overwritten.
+ *   B, nbatch  >= 0; either 0 is a no-op.
+ * The results are those of nbatch calls of leg_forward, bit for bit.  For
+ * LEG_SPLIT_FP16 plans of the Abel GEMM + transform, the batches run as a
+ * two-stage pipeline on two internal streams of the plan: the input split
+ * and the GEMM of batch b on a high-priority stream, the transform of batch
+ * b-1 on a low-priority one after batch b's split, so that the transform
+ * runs on the SMs the GEMM's CTA pairs leave free.  The GEMM results
+ * alternate between the plan's two G-sized workspaces (the forward's and the
+ * backward's).  Ordered after the work already on `stream`; later work on
+ * `stream` sees every batch complete.  Other plans, nbatch = 1 and calls on
+ * a stream being captured run the batches through leg_forward in order.
+ * Errors: those of leg_forward; LEG_ERR_INVALID_ARG for B < 0 or nbatch < 0.
+ */
+LEG_API int leg_forward_batches(leg_plan_t plan, const void *f, void *c, int B, int nbatch, cudaStream_t stream);
 
 /*
  * leg_forward_profiled -- leg_forward with CUDA events recorded on `stream`

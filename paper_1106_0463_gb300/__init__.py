@@ -72,6 +72,7 @@ def _load():
         "leg_plan_reserve": ([vp, i], i),
         "leg_plan_info": ([vp] + [ctypes.POINTER(i)] * 7, i),
         "leg_forward": ([vp, vp, vp, i, vp], i),
+        "leg_forward_batches": ([vp, vp, vp, i, i, vp], i),
         "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_backward": ([vp, vp, vp, i, vp], i),
         "leg_forward_noalloc": ([vp, vp, vp, i, vp], i),
@@ -275,6 +276,23 @@ class Plan:
             c = torch.empty((B, self.N), dtype=self.io_dtype, device=f.device)
         pc = _dev_tensor(c, self.io_dtype, (B, self.N), "c")
         _check(_lib.leg_forward(self._h, pf, pc, B, _stream(stream)))
+        return c
+
+    def forward_batches(self, f: torch.Tensor, c: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """leg_forward_batches: f of shape (nbatch, B, K) on the device, c of
+        shape (nbatch, B, N); the batches one after another, pipelined for
+        split-FP16 plans (each batch's transform beside the next one's GEMM)."""
+        if f.dim() != 3:
+            raise ValueError("f must have shape (nbatch, B, K)")
+        nb, B = f.shape[0], f.shape[1]
+        pf = _dev_tensor(f.view(nb * B, f.shape[2]) if f.is_contiguous() else f, self.io_dtype,
+                         (nb * B, self.K), "f")
+        if c is None:
+            c = torch.empty((nb, B, self.N), dtype=self.io_dtype, device=f.device)
+        if c.dim() != 3 or tuple(c.shape) != (nb, B, self.N):
+            raise ValueError("c must have shape (%d, %d, %d)" % (nb, B, self.N))
+        pc = _dev_tensor(c.view(nb * B, self.N) if c.is_contiguous() else c, self.io_dtype, (nb * B, self.N), "c")
+        _check(_lib.leg_forward_batches(self._h, pf, pc, B, nb, _stream(stream)))
         return c
 
     def forward_noalloc(self, f: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:

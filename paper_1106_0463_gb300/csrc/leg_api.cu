@@ -28,10 +28,35 @@ void free_workspace(leg_plan *p)
     p->ws_B = 0;
 }
 
+}  // namespace
+
+// leg_forward_batches: a high-priority stream for the input splits and GEMMs,
+// a low-priority one for the transforms, and the events between them.
+struct LegPipeState {
+    cudaStream_t hi = nullptr, lo = nullptr;
+    cudaEvent_t start = nullptr, gemm_done = nullptr, done = nullptr;
+    cudaEvent_t split[2] = {}, tf[2] = {};
+};
+
+namespace {
+
+void pipe_free(leg_plan *p)
+{
+    LegPipeState *q = p->pipe;
+    if (!q) return;
+    for (cudaEvent_t e : {q->start, q->gemm_done, q->done, q->split[0], q->split[1], q->tf[0], q->tf[1]})
+        if (e) cudaEventDestroy(e);
+    if (q->hi) cudaStreamDestroy(q->hi);
+    if (q->lo) cudaStreamDestroy(q->lo);
+    delete q;
+    p->pipe = nullptr;
+}
+
 void free_plan(leg_plan *p)
 {
     if (!p) return;
     leg_ragged_forget_plan(p);
+    pipe_free(p);
     for (auto &e : p->fwd)
         if (e.exec) cudaGraphExecDestroy(e.exec);
     if (p->cap) cudaStreamDestroy(p->cap);
@@ -480,6 +505,83 @@ extern "C" int leg_forward(leg_plan_t p, const void *f, void *c, int B, cudaStre
         return forward_impl(p, f, c, B, st, nullptr);
     }
     LEG_CUDA_TRY(cudaGraphLaunch(e->exec, st));
+    return LEG_OK;
+}
+
+namespace {
+int pipe_state(leg_plan *p, LegPipeState **out)
+{
+    if (!p->pipe) {
+        LegPipeState *q = new (std::nothrow) LegPipeState();
+        if (!q) return leg_set_error(LEG_ERR_OOM, "host allocation of the pipeline state failed");
+        p->pipe = q;
+        int least = 0, greatest = 0;
+        LEG_CUDA_TRY(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        LEG_CUDA_TRY(cudaStreamCreateWithPriority(&q->hi, cudaStreamNonBlocking, greatest));
+        LEG_CUDA_TRY(cudaStreamCreateWithPriority(&q->lo, cudaStreamNonBlocking, least));
+        for (cudaEvent_t *e : {&q->start, &q->gemm_done, &q->done, &q->split[0], &q->split[1], &q->tf[0], &q->tf[1]})
+            LEG_CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+    *out = p->pipe;
+    return LEG_OK;
+}
+}  // namespace
+
+// Batches one after another.  Split-FP16 plans (Abel GEMM + transform) run
+// as a two-stage pipeline: batch b's input split and GEMM go to a
+// high-priority stream and write G or, for odd b, the backward's G-sized
+// workspace; batch b-1's transform goes to a low-priority stream once batch
+// b's split is done, so the GEMM's CTA pairs take their SMs first and the
+// transform runs on the SMs the GEMM's tiles leave free.  Each kernel is the
+// one leg_forward launches for a batch of B, so results are leg_forward's
+// bit for bit.  Other plans, and calls on a stream being captured, loop
+// leg_forward.
+extern "C" int leg_forward_batches(leg_plan_t p, const void *f, void *c, int B, int nbatch, cudaStream_t st)
+{
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B < 0 || nbatch < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0 or nbatch < 0");
+    if (B == 0 || nbatch == 0) return LEG_OK;
+    if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
+    const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
+    const size_t fstride = eb * (size_t)B * p->K, cstride = eb * (size_t)B * p->N;
+    const char *fb = static_cast<const char *>(f);
+    char *cb = static_cast<char *>(c);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (p->dtype != LEG_SPLIT_FP16 || p->collapsed() || nbatch == 1 || cs != cudaStreamCaptureStatusNone) {
+        for (int b = 0; b < nbatch; ++b)
+            if ((rc = leg_forward(p, fb + fstride * b, cb + cstride * b, B, st))) return rc;
+        return LEG_OK;
+    }
+    if ((rc = ensure_workspace(p, B))) return rc;
+    LegPipeState *q = nullptr;
+    if ((rc = pipe_state(p, &q))) return rc;
+    const LegSplitIn in = leg_split_workspace(p);
+    float2 *Gs[2] = {static_cast<float2 *>(p->G), static_cast<float2 *>(p->Gbar)};
+    LEG_CUDA_TRY(cudaEventRecord(q->start, st));   // after the work already on `stream`
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->start, 0));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->start, 0));
+    for (int b = 0; b < nbatch; ++b) {
+        const int s = b & 1;
+        if (b >= 2) LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->tf[s], 0));   // batch b-2's transform read Gs[s]
+        rc = leg_split_prepare_input_into(p, reinterpret_cast<const float *>(fb + fstride * b), B, in, Gs[s],
+                                          p->ldg, q->hi);
+        if (rc) return rc;
+        LEG_CUDA_TRY(cudaEventRecord(q->split[s], q->hi));
+        if (b >= 1) {   // batch b-1's GEMM is done (it precedes this split on hi)
+            LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->split[s], 0));
+            if ((rc = leg_fft_forward(p, Gs[s ^ 1], p->ldg, cb + cstride * (b - 1), B, q->lo))) return rc;
+            LEG_CUDA_TRY(cudaEventRecord(q->tf[s ^ 1], q->lo));
+        }
+        if ((rc = leg_gemm_split_fwd_into(p, B, in, Gs[s], p->ldg, q->hi))) return rc;
+    }
+    LEG_CUDA_TRY(cudaEventRecord(q->gemm_done, q->hi));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->gemm_done, 0));
+    const int l = (nbatch - 1) & 1;
+    if ((rc = leg_fft_forward(p, Gs[l], p->ldg, cb + cstride * (nbatch - 1), B, q->lo))) return rc;
+    LEG_CUDA_TRY(cudaEventRecord(q->done, q->lo));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(st, q->done, 0));   // later work on `stream` sees every batch
     return LEG_OK;
 }
 

@@ -80,6 +80,7 @@ constexpr int LEG_SPLIT_NF = 7;
 // Plan.
 // ---------------------------------------------------------------------------
 struct LegHostState;                  // leg_forward_host's device copies, streams, events (leg_host.cu)
+struct LegPipeState;                  // leg_forward_batches' streams and events (leg_api.cu)
 constexpr int LEG_HOST_CHUNKS = 4;     // pieces of a leg_forward_host batch (split-FP16 plans)
 
 struct leg_plan {
@@ -137,6 +138,7 @@ struct leg_plan {
     int *fexp = nullptr;                          // per-function power-of-two scale
     void *Gbar = nullptr;     // backward: B x ldg (FP64 for LEG_F64, FP32 otherwise)
     LegHostState *host = nullptr;   // created by the first leg_forward_host
+    LegPipeState *pipe = nullptr;   // created by the first pipelined leg_forward_batches
 
     // leg_forward replays a CUDA graph of its launches when called again with
     // the same buffers and launch parameters (the key); captured on `cap`.

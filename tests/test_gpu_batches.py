@@ -1,0 +1,83 @@
+"""leg_forward_batches: batches one after another, pipelined for split-FP16
+plans (batch b's split and GEMM on a high-priority stream, batch b-1's
+transform on a low-priority one, the GEMM results alternating between two
+G-sized workspaces).  Every batch must equal leg_forward on it bit for bit,
+whatever the number of batches, the batch size, the transform kernel, and for
+the plans that take the plain loop (FP64, collapsed); the backward pass, whose
+workspace the pipeline borrows, must be unaffected.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def leg():
+    import paper_1106_0463_gb300 as leg
+    assert torch.cuda.is_available()
+    return leg
+
+
+def batches(nb, B, K, seed, dtype=torch.float32):
+    f, _, _ = workloads.random_chebyshev(nb * B, K, (0.8, 0.99), np.random.default_rng(seed))
+    return torch.from_numpy(f).to(dtype).view(nb, B, K).cuda()
+
+
+@pytest.mark.parametrize("transform", ["sine", "reg"])
+def test_batches_equal_forward(leg, transform):
+    N, M, K = 384, 1024, 513
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    plan.set_transform(leg.TRANSFORM_SINE if transform == "sine" else leg.TRANSFORM_REG)
+    for nb, B in ((1, 40), (2, 300), (3, 37), (6, 129)):
+        f = batches(nb, B, K, nb * 1000 + B)
+        c = torch.full((nb, B, N), float("nan"), device="cuda")
+        plan.forward_batches(f, c)
+        for b in range(nb):
+            ref = plan.forward(f[b].contiguous())
+            assert torch.equal(c[b], ref), (nb, B, b)
+    plan.status()
+
+
+def test_batches_headline_shape(leg):
+    """The headline shape (K = 8193, M = 16384, 256 functions per batch):
+    three pipelined batches against leg_forward on each."""
+    N, M, K, B, nb = 4096, 16384, 8193, 256, 3
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    f = batches(nb, B, K, 5)
+    c = plan.forward_batches(f)
+    for b in range(nb):
+        assert torch.equal(c[b], plan.forward(f[b].contiguous())), b
+    plan.status()
+
+
+@pytest.mark.parametrize("dt,flags", [(0, 0), (3, 2), (1, 0)])
+def test_batches_other_plans_loop(leg, dt, flags):
+    N, M, K, B, nb = 96, 256, 129, 50, 3
+    plan = leg.Plan(N, M, K, 0, dt, flags=flags)
+    f = batches(nb, B, K, 11, plan.io_dtype)
+    c = plan.forward_batches(f)
+    for b in range(nb):
+        assert torch.equal(c[b], plan.forward(f[b].contiguous())), b
+
+
+def test_backward_unaffected_by_the_pipeline(leg):
+    N, M, K, B = 256, 1024, 513, 64
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    dc = torch.randn(B, N, device="cuda")
+    before = plan.backward(dc).clone()
+    plan.forward_batches(batches(4, B, K, 21))
+    assert torch.equal(plan.backward(dc), before)
+
+
+def test_batches_argument_errors(leg):
+    plan = leg.Plan(32, 128, 33, 0, leg.SPLIT_FP16)
+    f = torch.zeros((2, 4, 33), device="cuda")
+    c = torch.zeros((2, 4, 32), device="cuda")
+    assert leg._lib.leg_forward_batches(plan._h, f.data_ptr(), c.data_ptr(), 4, -1, None) == 1
+    assert leg._lib.leg_forward_batches(plan._h, f.data_ptr(), c.data_ptr(), 4, 0, None) == 0
+    with pytest.raises(ValueError):
+        plan.forward_batches(f[0])
