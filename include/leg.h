@@ -513,6 +513,31 @@ LEG_API int leg_forward_host(leg_plan_t plan, const void *f_host, void *c_host, 
 LEG_API int leg_plan_set_host_overlap(leg_plan_t plan, int on);
 
 /*
+ * leg_forward_host_batches -- leg_forward_host on nbatch batches of B
+ * functions, one after another.  (A library convenience with no counterpart
+ * in the paper.)
+ *   f_host  host, nbatch x B x K (FP64 for LEG_F64, FP32 otherwise);
+ *   c_host  host, nbatch x B x N (same type); overwritten.
+ *   B, nbatch  >= 0; either 0 is a no-op.
+ * For LEG_SPLIT_FP16 plans of the Abel GEMM + transform with page-locked,
+ * mapped host buffers, the batches run through the pipeline of
+ * leg_forward_batches, and each batch's input is copied by a copy engine into
+ * one of the plan's two staging buffers (2 x B x K FP32 values, allocated by
+ * the first call that needs them, which synchronises the device): the first
+ * copy after the work already on `stream`, each later one while the kernels
+ * of the batches before it run; each batch's transform writes its
+ * coefficients into c_host in place.  Other plans and buffers, nbatch = 1 and
+ * calls on a stream being captured run leg_forward_host on each batch in
+ * turn.  Results equal leg_forward's bit for bit.  c_host is complete once
+ * `stream` has reached the end of the call; both buffers must stay valid
+ * until then.
+ * Errors: those of leg_forward_host; LEG_ERR_INVALID_ARG for B < 0 or
+ * nbatch < 0.
+ */
+LEG_API int leg_forward_host_batches(leg_plan_t plan, const void *f_host, void *c_host, int B, int nbatch,
+                                     cudaStream_t stream);
+
+/*
  * leg_memory_info -- device memory the library holds at this moment for the
  * objects it created (plans and their workspaces, ragged batches, the
  * host-buffer path's copies, cached one-call batches): the number of live

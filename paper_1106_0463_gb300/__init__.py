@@ -73,6 +73,7 @@ def _load():
         "leg_plan_info": ([vp] + [ctypes.POINTER(i)] * 7, i),
         "leg_forward": ([vp, vp, vp, i, vp], i),
         "leg_forward_batches": ([vp, vp, vp, i, i, vp], i),
+        "leg_forward_host_batches": ([vp, vp, vp, i, i, vp], i),
         "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_backward": ([vp, vp, vp, i, vp], i),
         "leg_forward_noalloc": ([vp, vp, vp, i, vp], i),
@@ -320,6 +321,29 @@ class Plan:
         pc = _host_tensor(c_host, self.io_dtype, (B, self.N), "c_host")
         st = _stream(stream)
         _check(_lib.leg_forward_host(self._h, pf, pc, B, st))
+        if sync:
+            (stream or torch.cuda.current_stream()).synchronize()
+        return c_host
+
+    def forward_host_batches(self, f_host: torch.Tensor, c_host: torch.Tensor | None = None, stream=None,
+                             sync: bool = True) -> torch.Tensor:
+        """leg_forward_host_batches: f_host (nbatch, B, K) and c_host (nbatch, B,
+        N) on the CPU, ideally pinned (c_host pinned and allocated when None);
+        pipelined for split-FP16 plans.  With sync=False the call returns at
+        once and c_host is complete when the stream has reached it."""
+        if f_host.dim() != 3:
+            raise ValueError("f_host must have shape (nbatch, B, K)")
+        nb, B = f_host.shape[0], f_host.shape[1]
+        pf = _host_tensor(f_host.view(nb * B, -1) if f_host.is_contiguous() else f_host, self.io_dtype,
+                          (nb * B, self.K), "f_host")
+        if c_host is None:
+            c_host = torch.empty((nb, B, self.N), dtype=self.io_dtype).pin_memory()
+        if c_host.dim() != 3 or tuple(c_host.shape) != (nb, B, self.N):
+            raise ValueError("c_host must have shape (%d, %d, %d)" % (nb, B, self.N))
+        pc = _host_tensor(c_host.view(nb * B, self.N) if c_host.is_contiguous() else c_host, self.io_dtype,
+                          (nb * B, self.N), "c_host")
+        st = _stream(stream)
+        _check(_lib.leg_forward_host_batches(self._h, pf, pc, B, nb, st))
         if sync:
             (stream or torch.cuda.current_stream()).synchronize()
         return c_host

@@ -527,15 +527,63 @@ int pipe_state(leg_plan *p, LegPipeState **out)
 }
 }  // namespace
 
-// Batches one after another.  Split-FP16 plans (Abel GEMM + transform) run
-// as a two-stage pipeline: batch b's input split and GEMM go to a
-// high-priority stream and write G or, for odd b, the backward's G-sized
-// workspace; batch b-1's transform goes to a low-priority stream once batch
-// b's split is done, so the GEMM's CTA pairs take their SMs first and the
-// transform runs on the SMs the GEMM's tiles leave free.  Each kernel is the
-// one leg_forward launches for a batch of B, so results are leg_forward's
-// bit for bit.  Other plans, and calls on a stream being captured, loop
-// leg_forward.
+// The split-FP16 pipeline over nbatch batches: batch b's input split and
+// GEMM go to a high-priority stream and write G or, for odd b, the backward's
+// G-sized workspace; batch b-1's transform goes to a low-priority stream once
+// batch b's split is done, so the GEMM's CTA pairs take their SMs first and
+// the transform runs on the SMs the GEMM's tiles leave free.  Batch b's split
+// waits for batch b-2's transform (the last reader of its G buffer).  Each
+// kernel is the one leg_forward launches for a batch of B.  With io.stage,
+// batch b's input is first copied from io.f (host) into staging buffer b % 2
+// on io.copy, after the split that last read that buffer.
+int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cudaStream_t st)
+{
+    int rc = ensure_workspace(p, B);
+    if (rc) return rc;
+    LegPipeState *q = nullptr;
+    if ((rc = pipe_state(p, &q))) return rc;
+    const LegSplitIn in = leg_split_workspace(p);
+    float2 *Gs[2] = {static_cast<float2 *>(p->G), static_cast<float2 *>(p->Gbar)};
+    const char *fb = static_cast<const char *>(io.f);
+    char *cb = static_cast<char *>(io.c);
+    LEG_CUDA_TRY(cudaEventRecord(q->start, st));   // after the work already on `stream`
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->start, 0));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->start, 0));
+    if (io.stage[0]) LEG_CUDA_TRY(cudaStreamWaitEvent(io.copy, q->start, 0));
+    for (int b = 0; b < nbatch; ++b) {
+        const int s = b & 1;
+        const float *fin = reinterpret_cast<const float *>(fb + io.fstride * b);
+        if (io.stage[0]) {
+            // a never-recorded event counts as completed: the first uses wait for nothing
+            LEG_CUDA_TRY(cudaStreamWaitEvent(io.copy, io.stage_free[s], 0));
+            LEG_CUDA_TRY(cudaMemcpyAsync(io.stage[s], fin, io.fstride, cudaMemcpyHostToDevice, io.copy));
+            LEG_CUDA_TRY(cudaEventRecord(io.stage_ready[s], io.copy));
+            LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, io.stage_ready[s], 0));
+            fin = static_cast<const float *>(io.stage[s]);
+        }
+        if (b >= 2) LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->tf[s], 0));   // batch b-2's transform read Gs[s]
+        if ((rc = leg_split_prepare_input_into(p, fin, B, in, Gs[s], p->ldg, q->hi))) return rc;
+        LEG_CUDA_TRY(cudaEventRecord(q->split[s], q->hi));
+        if (io.stage[0]) LEG_CUDA_TRY(cudaEventRecord(io.stage_free[s], q->hi));
+        if (b >= 1) {   // batch b-1's GEMM is done (it precedes this split on hi)
+            LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->split[s], 0));
+            if ((rc = leg_fft_forward(p, Gs[s ^ 1], p->ldg, cb + io.cstride * (b - 1), B, q->lo))) return rc;
+            LEG_CUDA_TRY(cudaEventRecord(q->tf[s ^ 1], q->lo));
+        }
+        if ((rc = leg_gemm_split_fwd_into(p, B, in, Gs[s], p->ldg, q->hi))) return rc;
+    }
+    LEG_CUDA_TRY(cudaEventRecord(q->gemm_done, q->hi));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->gemm_done, 0));
+    const int l = (nbatch - 1) & 1;
+    if ((rc = leg_fft_forward(p, Gs[l], p->ldg, cb + io.cstride * (nbatch - 1), B, q->lo))) return rc;
+    LEG_CUDA_TRY(cudaEventRecord(q->done, q->lo));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(st, q->done, 0));   // later work on `stream` sees every batch
+    return LEG_OK;
+}
+
+// Batches one after another: the pipeline above for split-FP16 plans of the
+// Abel GEMM + transform, results those of leg_forward bit for bit; other
+// plans, a single batch and calls on a stream being captured loop leg_forward.
 extern "C" int leg_forward_batches(leg_plan_t p, const void *f, void *c, int B, int nbatch, cudaStream_t st)
 {
     int rc = check_plan(p);
@@ -544,46 +592,24 @@ extern "C" int leg_forward_batches(leg_plan_t p, const void *f, void *c, int B, 
     if (B == 0 || nbatch == 0) return LEG_OK;
     if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
     const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
-    const size_t fstride = eb * (size_t)B * p->K, cstride = eb * (size_t)B * p->N;
-    const char *fb = static_cast<const char *>(f);
-    char *cb = static_cast<char *>(c);
+    LegPipeIO io;
+    io.f = f;
+    io.c = c;
+    io.fstride = eb * (size_t)B * p->K;
+    io.cstride = eb * (size_t)B * p->N;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
-    if (p->dtype != LEG_SPLIT_FP16 || p->collapsed() || nbatch == 1 || cs != cudaStreamCaptureStatusNone) {
+    if (!leg_pipeline_applies(p) || nbatch == 1 || cs != cudaStreamCaptureStatusNone) {
         for (int b = 0; b < nbatch; ++b)
-            if ((rc = leg_forward(p, fb + fstride * b, cb + cstride * b, B, st))) return rc;
+            if ((rc = leg_forward(p, static_cast<const char *>(f) + io.fstride * b,
+                                  static_cast<char *>(c) + io.cstride * b, B, st)))
+                return rc;
         return LEG_OK;
     }
-    if ((rc = ensure_workspace(p, B))) return rc;
-    LegPipeState *q = nullptr;
-    if ((rc = pipe_state(p, &q))) return rc;
-    const LegSplitIn in = leg_split_workspace(p);
-    float2 *Gs[2] = {static_cast<float2 *>(p->G), static_cast<float2 *>(p->Gbar)};
-    LEG_CUDA_TRY(cudaEventRecord(q->start, st));   // after the work already on `stream`
-    LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->start, 0));
-    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->start, 0));
-    for (int b = 0; b < nbatch; ++b) {
-        const int s = b & 1;
-        if (b >= 2) LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->tf[s], 0));   // batch b-2's transform read Gs[s]
-        rc = leg_split_prepare_input_into(p, reinterpret_cast<const float *>(fb + fstride * b), B, in, Gs[s],
-                                          p->ldg, q->hi);
-        if (rc) return rc;
-        LEG_CUDA_TRY(cudaEventRecord(q->split[s], q->hi));
-        if (b >= 1) {   // batch b-1's GEMM is done (it precedes this split on hi)
-            LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->split[s], 0));
-            if ((rc = leg_fft_forward(p, Gs[s ^ 1], p->ldg, cb + cstride * (b - 1), B, q->lo))) return rc;
-            LEG_CUDA_TRY(cudaEventRecord(q->tf[s ^ 1], q->lo));
-        }
-        if ((rc = leg_gemm_split_fwd_into(p, B, in, Gs[s], p->ldg, q->hi))) return rc;
-    }
-    LEG_CUDA_TRY(cudaEventRecord(q->gemm_done, q->hi));
-    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->gemm_done, 0));
-    const int l = (nbatch - 1) & 1;
-    if ((rc = leg_fft_forward(p, Gs[l], p->ldg, cb + cstride * (nbatch - 1), B, q->lo))) return rc;
-    LEG_CUDA_TRY(cudaEventRecord(q->done, q->lo));
-    LEG_CUDA_TRY(cudaStreamWaitEvent(st, q->done, 0));   // later work on `stream` sees every batch
-    return LEG_OK;
+    return leg_pipeline_split(p, B, nbatch, io, st);
 }
+
+bool leg_pipeline_applies(const leg_plan *p) { return p->dtype == LEG_SPLIT_FP16 && !p->collapsed(); }
 
 extern "C" int leg_forward_profiled(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, float *ms)
 {

@@ -121,6 +121,33 @@ const void *device_view(const void *host)
     return a.devicePointer;
 }
 
+// Two staging buffers of B input rows each (grown on demand; growing
+// synchronises the device).
+int ensure_stage(LegHostState *h, const leg_plan *p, int B)
+{
+    if (B <= h->stage_cap) return LEG_OK;
+    LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
+    for (int i = 0; i < 2; ++i) {
+        leg_dev_free(h->stage[i]);
+        h->stage[i] = nullptr;
+    }
+    h->stage_cap = 0;
+    const size_t bytes = sizeof(float) * (size_t)B * p->K;
+    for (int i = 0; i < 2; ++i) {
+        const cudaError_t e = leg_dev_malloc(&h->stage[i], bytes);
+        if (e != cudaSuccess) {   // release what was taken: nothing stays half-grown
+            for (int j = 0; j < 2; ++j) {
+                leg_dev_free(h->stage[j]);
+                h->stage[j] = nullptr;
+            }
+            return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
+                                 std::string("leg_forward_host staging buffers: ") + cudaGetErrorString(e));
+        }
+    }
+    h->stage_cap = B;
+    return LEG_OK;
+}
+
 // Host overlap: the input goes to staging buffer `slot` by a copy on the
 // internal stream that waits only for the previous call that used the same
 // buffer to finish; the kernels read it there and write c in place (cv).
@@ -129,27 +156,8 @@ int forward_staged(leg_plan *p, const void *f_host, void *cv, int B, cudaStream_
     LegHostState *h = nullptr;
     int rc = host_base(p, &h);
     if (rc) return rc;
+    if ((rc = ensure_stage(h, p, B))) return rc;
     const size_t bytes = sizeof(float) * (size_t)B * p->K;
-    if (B > h->stage_cap) {
-        LEG_CUDA_TRY(cudaDeviceSynchronize());   // earlier calls may still use the old buffers
-        for (int i = 0; i < 2; ++i) {
-            leg_dev_free(h->stage[i]);
-            h->stage[i] = nullptr;
-        }
-        h->stage_cap = 0;
-        for (int i = 0; i < 2; ++i) {
-            const cudaError_t e = leg_dev_malloc(&h->stage[i], bytes);
-            if (e != cudaSuccess) {   // release what was taken: nothing stays half-grown
-                for (int j = 0; j < 2; ++j) {
-                    leg_dev_free(h->stage[j]);
-                    h->stage[j] = nullptr;
-                }
-                return leg_set_error(e == cudaErrorMemoryAllocation ? LEG_ERR_OOM : LEG_ERR_CUDA,
-                                     std::string("leg_forward_host staging buffers: ") + cudaGetErrorString(e));
-            }
-        }
-        h->stage_cap = B;
-    }
     const int s = h->slot;
     // a never-recorded event counts as completed: the first use waits for nothing
     LEG_CUDA_TRY(cudaStreamWaitEvent(h->h2d, h->stage_free[s], 0));
@@ -251,5 +259,55 @@ extern "C" int leg_forward_host(leg_plan_t p, const void *f_host, void *c_host, 
     // later work on `stream` (and a synchronisation of it) sees c_host complete
     LEG_CUDA_TRY(cudaEventRecord(h->done, h->d2h));
     LEG_CUDA_TRY(cudaStreamWaitEvent(st, h->done, 0));
+    return LEG_OK;
+}
+
+// Batches on host buffers.  Split-FP16 plans with pinned, mapped buffers run
+// the batch pipeline of leg_forward_batches with each batch's input copied
+// by a copy engine into one of the two staging buffers (the first copy after
+// the work already on `stream`, each later one during the kernels of the
+// batches before it) and each batch's coefficients written into c_host in
+// place by its transform.  Otherwise the batches go through
+// leg_forward_host in turn.
+extern "C" int leg_forward_host_batches(leg_plan_t p, const void *f_host, void *c_host, int B, int nbatch,
+                                        cudaStream_t st)
+{
+    if (!p) return leg_set_error(LEG_ERR_INVALID_ARG, "plan is NULL");
+    if (B < 0 || nbatch < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0 or nbatch < 0");
+    if (B == 0 || nbatch == 0) return LEG_OK;
+    if (!f_host || !c_host) return leg_set_error(LEG_ERR_INVALID_ARG, "null f_host or c_host");
+    int dev = -1;
+    LEG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != p->device) return leg_set_error(LEG_ERR_INVALID_ARG, "current device differs from the plan's device");
+    int rc = leg_plan_reserve(p, B);
+    if (rc) return rc;
+    const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
+    LegPipeIO io;
+    io.f = f_host;
+    io.fstride = eb * (size_t)B * p->K;
+    io.cstride = eb * (size_t)B * p->N;
+    if (leg_pipeline_applies(p) && nbatch > 1) {
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+        void *cv = const_cast<void *>(device_view(c_host));
+        if (cs == cudaStreamCaptureStatusNone && device_view(f_host) && cv) {
+            LegHostState *h = nullptr;
+            if ((rc = host_base(p, &h))) return rc;
+            if ((rc = ensure_stage(h, p, B))) return rc;
+            io.c = cv;
+            io.copy = h->h2d;
+            for (int i = 0; i < 2; ++i) {
+                io.stage[i] = h->stage[i];
+                io.stage_ready[i] = h->stage_ready[i];
+                io.stage_free[i] = h->stage_free[i];
+            }
+            return leg_pipeline_split(p, B, nbatch, io, st);
+        }
+    }
+    for (int b = 0; b < nbatch; ++b) {
+        rc = leg_forward_host(p, static_cast<const char *>(f_host) + io.fstride * b,
+                              static_cast<char *>(c_host) + io.cstride * b, B, st);
+        if (rc) return rc;
+    }
     return LEG_OK;
 }

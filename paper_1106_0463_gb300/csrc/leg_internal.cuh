@@ -171,6 +171,20 @@ struct leg_plan {
 };
 
 void leg_host_free(leg_plan *p);
+
+// Sources and sinks of the split-FP16 batch pipeline (leg_api.cu): batch b
+// reads f + b fstride (device-readable, or host memory copied into
+// stage[b % 2] on `copy` when stage[0] is set) and writes c + b cstride.
+struct LegPipeIO {
+    const void *f = nullptr;
+    void *c = nullptr;
+    size_t fstride = 0, cstride = 0;   // bytes per batch
+    void *stage[2] = {};
+    cudaStream_t copy = nullptr;
+    cudaEvent_t stage_ready[2] = {}, stage_free[2] = {};
+};
+int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cudaStream_t st);
+bool leg_pipeline_applies(const leg_plan *p);
 // drops the one-call ragged batches built over plan p (leg_ragged.cu)
 void leg_ragged_forget_plan(const leg_plan *p);
 

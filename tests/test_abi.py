@@ -73,6 +73,7 @@ def test_every_handle_entry_point_rejects_null_without_a_gpu(libpath):
         "leg_plan_tile_info": ([vp, i, vp, vp, vp], (None, 4, None, None, None)),
         "leg_plan_autotune": ([vp, vp, vp, i, vp, vp, vp], (None, None, None, 4, None, None, None)),
         "leg_forward_host": ([vp, vp, vp, i, vp], (None, None, None, 4, None)),
+        "leg_forward_host_batches": ([vp, vp, vp, i, i, vp], (None, None, None, 4, 2, None)),
         "leg_forward_noalloc": ([vp, vp, vp, i, vp], (None, None, None, 4, None)),
         "leg_forward_ragged": ([vp, vp, vp, vp], (None, None, None, None)),
         "leg_ragged_status": ([vp, i], (None, 0)),

@@ -81,3 +81,34 @@ def test_batches_argument_errors(leg):
     assert leg._lib.leg_forward_batches(plan._h, f.data_ptr(), c.data_ptr(), 4, 0, None) == 0
     with pytest.raises(ValueError):
         plan.forward_batches(f[0])
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_batches_equal_forward(leg, pinned):
+    """leg_forward_host_batches: pinned buffers take the pipeline with staged
+    input copies and in-place output writes, pageable ones the loop of
+    leg_forward_host; both equal leg_forward on each batch bit for bit,
+    including calls queued back to back without synchronising."""
+    N, M, K = 256, 1024, 513
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    for nb, B in ((2, 64), (5, 37), (3, 300)):
+        fd = batches(nb, B, K, 300 + nb * B)
+        refs = [plan.forward(fd[b].contiguous()).cpu() for b in range(nb)]
+        fh = fd.cpu()
+        ch = torch.full((nb, B, N), float("nan"))
+        if pinned:
+            fh, ch = fh.pin_memory(), ch.pin_memory()
+        plan.forward_host_batches(fh, ch, sync=False)
+        plan.forward_host_batches(fh, ch)
+        for b in range(nb):
+            assert torch.equal(ch[b], refs[b]), (nb, B, b)
+    plan.status()
+
+
+def test_host_batches_fp64_loop(leg):
+    N, M, K, B, nb = 64, 256, 65, 20, 3
+    plan = leg.Plan(N, M, K, 0, leg.F64)
+    fd = batches(nb, B, K, 17, torch.float64)
+    c = plan.forward_host_batches(fd.cpu().pin_memory())
+    for b in range(nb):
+        assert torch.equal(c[b], plan.forward(fd[b].contiguous()).cpu()), b
