@@ -1063,6 +1063,23 @@ def gpu_arm(args, rank, world, local_rank):
         sub["split_fp16"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src, warm_steps=50))
         sub["split_fp16_sine_form"] = strip(c2.run("split_fp16", flush, 50, 3, peaks, peak_src,
                                                    transform=leg.TRANSFORM_SINE))
+        # the same as a stream of 20 batches (distinct buffers, 336 MB) through leg_forward_batches
+        p2, nb2 = c2.plan("split_fp16"), 20
+        fb2 = c2.inputs("split_fp16").unsqueeze(0).expand(nb2, -1, -1).contiguous()
+        cb2 = torch.empty((nb2, c2.B, c2.N), dtype=torch.float32, device="cuda")
+        p2.forward_batches(fb2[:3], cb2[:3])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        p2.forward_batches(fb2, cb2)
+        e1.record()
+        e1.synchronize()
+        ms2 = e0.elapsed_time(e1) / nb2
+        sub["split_fp16_sine_form_batches"] = {
+            "value": c2.B * c2.N / (ms2 / 1e3), "ms_per_step": ms2, "batches": nb2,
+            "api": "leg_forward_batches (each batch's transform beside the next batch's split and GEMM)",
+            "bit_identical_to_leg_forward": bool(torch.equal(cb2[nb2 - 1], p2.forward(fb2[nb2 - 1])))}
+        del fb2, cb2
         sub["f32"] = strip(c2.run("f32", flush, 20, 3, peaks, peak_src))
         sub["f32_sine_form"] = strip(c2.run("f32", flush, 20, 3, peaks, peak_src, transform=leg.TRANSFORM_SINE))
         sub["f64"] = strip(c2.run("f64", flush, 3, 1, peaks, peak_src))
