@@ -207,6 +207,20 @@ LEG_API int leg_forward(leg_plan_t plan, const void *f, void *c, int B, cudaStre
 LEG_API int leg_forward_batches(leg_plan_t plan, const void *f, void *c, int B, int nbatch, cudaStream_t stream);
 
 /*
+ * leg_forward_batches_profiled -- leg_forward_batches that also returns the
+ * mean time per batch (milliseconds) of each stage: ms[0] the input
+ * preparation, ms[1] the GEMM, ms[2] the transform, taken with CUDA events on
+ * the stage's own stream inside the pipeline (for pipelined plans; other
+ * plans and nbatch = 1 average leg_forward_profiled over the batches).  The
+ * events between the stages change the launch chaining slightly, so the
+ * stage times are for the roofline figures, not for the throughput.
+ * Synchronises `stream`; LEG_ERR_INVALID_ARG on a stream being captured or
+ * for a NULL ms.  Otherwise as leg_forward_batches.
+ */
+LEG_API int leg_forward_batches_profiled(leg_plan_t plan, const void *f, void *c, int B, int nbatch,
+                                         cudaStream_t stream, float *ms);
+
+/*
  * leg_forward_profiled -- leg_forward with CUDA events recorded on `stream`
  * between its stages.  Blocks the host until the pass completes, then writes
  * the stage durations in milliseconds: ms[0] input preparation (split or

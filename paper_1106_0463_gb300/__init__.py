@@ -73,6 +73,7 @@ def _load():
         "leg_plan_info": ([vp] + [ctypes.POINTER(i)] * 7, i),
         "leg_forward": ([vp, vp, vp, i, vp], i),
         "leg_forward_batches": ([vp, vp, vp, i, i, vp], i),
+        "leg_forward_batches_profiled": ([vp, vp, vp, i, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_forward_host_batches": ([vp, vp, vp, i, i, vp], i),
         "leg_forward_profiled": ([vp, vp, vp, i, vp, ctypes.POINTER(ctypes.c_float)], i),
         "leg_backward": ([vp, vp, vp, i, vp], i),
@@ -295,6 +296,17 @@ class Plan:
         pc = _dev_tensor(c.view(nb * B, self.N) if c.is_contiguous() else c, self.io_dtype, (nb * B, self.N), "c")
         _check(_lib.leg_forward_batches(self._h, pf, pc, B, nb, _stream(stream)))
         return c
+
+    def forward_batches_profiled(self, f: torch.Tensor, c: torch.Tensor, stream=None):
+        """leg_forward_batches_profiled: the pipelined batches with the mean
+        time per batch of each stage inside the pipeline; synchronises.
+        Returns (prep_ms, gemm_ms, fft_ms)."""
+        nb, B = f.shape[0], f.shape[1]
+        pf = _dev_tensor(f.view(nb * B, -1), self.io_dtype, (nb * B, self.K), "f")
+        pc = _dev_tensor(c.view(nb * B, -1), self.io_dtype, (nb * B, self.N), "c")
+        ms = (ctypes.c_float * 3)()
+        _check(_lib.leg_forward_batches_profiled(self._h, pf, pc, B, nb, _stream(stream), ms))
+        return tuple(float(v) for v in ms)
 
     def forward_noalloc(self, f: torch.Tensor, c: torch.Tensor, stream=None) -> torch.Tensor:
         """leg_forward_noalloc: the split-FP16 forward pass for callers that

@@ -6,6 +6,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <vector>
 
 #include "leg_internal.cuh"
 
@@ -562,20 +563,27 @@ int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cuda
             fin = static_cast<const float *>(io.stage[s]);
         }
         if (b >= 2) LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->tf[s], 0));   // batch b-2's transform read Gs[s]
+        if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * b], q->hi));
         if ((rc = leg_split_prepare_input_into(p, fin, B, in, Gs[s], p->ldg, q->hi))) return rc;
         LEG_CUDA_TRY(cudaEventRecord(q->split[s], q->hi));
+        if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * b + 1], q->hi));
         if (io.stage[0]) LEG_CUDA_TRY(cudaEventRecord(io.stage_free[s], q->hi));
         if (b >= 1) {   // batch b-1's GEMM is done (it precedes this split on hi)
             LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->split[s], 0));
+            if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (b - 1) + 3], q->lo));
             if ((rc = leg_fft_forward(p, Gs[s ^ 1], p->ldg, cb + io.cstride * (b - 1), B, q->lo))) return rc;
             LEG_CUDA_TRY(cudaEventRecord(q->tf[s ^ 1], q->lo));
+            if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (b - 1) + 4], q->lo));
         }
         if ((rc = leg_gemm_split_fwd_into(p, B, in, Gs[s], p->ldg, q->hi))) return rc;
+        if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * b + 2], q->hi));
     }
     LEG_CUDA_TRY(cudaEventRecord(q->gemm_done, q->hi));
     LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->gemm_done, 0));
     const int l = (nbatch - 1) & 1;
+    if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (nbatch - 1) + 3], q->lo));
     if ((rc = leg_fft_forward(p, Gs[l], p->ldg, cb + io.cstride * (nbatch - 1), B, q->lo))) return rc;
+    if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (nbatch - 1) + 4], q->lo));
     LEG_CUDA_TRY(cudaEventRecord(q->done, q->lo));
     LEG_CUDA_TRY(cudaStreamWaitEvent(st, q->done, 0));   // later work on `stream` sees every batch
     return LEG_OK;
@@ -610,6 +618,65 @@ extern "C" int leg_forward_batches(leg_plan_t p, const void *f, void *c, int B, 
 }
 
 bool leg_pipeline_applies(const leg_plan *p) { return p->dtype == LEG_SPLIT_FP16 && !p->collapsed(); }
+
+// leg_forward_batches with the mean time of each stage per batch, taken with
+// events on the stage's own stream inside the pipeline (or averaged over
+// leg_forward_profiled calls where there is no pipeline); synchronises.
+extern "C" int leg_forward_batches_profiled(leg_plan_t p, const void *f, void *c, int B, int nbatch,
+                                            cudaStream_t st, float *ms)
+{
+    if (!ms) return leg_set_error(LEG_ERR_INVALID_ARG, "ms is NULL");
+    int rc = check_plan(p);
+    if (rc) return rc;
+    if (B < 0 || nbatch < 0) return leg_set_error(LEG_ERR_INVALID_ARG, "B < 0 or nbatch < 0");
+    ms[0] = ms[1] = ms[2] = 0.0f;
+    if (B == 0 || nbatch == 0) return LEG_OK;
+    if (!f || !c) return leg_set_error(LEG_ERR_INVALID_ARG, "null f or c");
+    const size_t eb = (p->dtype == LEG_F64) ? sizeof(double) : sizeof(float);
+    LegPipeIO io;
+    io.f = f;
+    io.c = c;
+    io.fstride = eb * (size_t)B * p->K;
+    io.cstride = eb * (size_t)B * p->N;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    LEG_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+    if (cs != cudaStreamCaptureStatusNone)
+        return leg_set_error(LEG_ERR_INVALID_ARG, "leg_forward_batches_profiled synchronises: not on a capturing stream");
+    if (!leg_pipeline_applies(p) || nbatch == 1) {
+        for (int b = 0; b < nbatch; ++b) {
+            float t[3];
+            rc = leg_forward_profiled(p, static_cast<const char *>(f) + io.fstride * b,
+                                      static_cast<char *>(c) + io.cstride * b, B, st, t);
+            if (rc) return rc;
+            for (int i = 0; i < 3; ++i) ms[i] += t[i] / nbatch;
+        }
+        return LEG_OK;
+    }
+    std::vector<cudaEvent_t> ev(5 * (size_t)nbatch, nullptr);
+    cudaError_t e = cudaSuccess;
+    for (auto &x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
+    if (e == cudaSuccess) {
+        io.prof = ev.data();
+        rc = leg_pipeline_split(p, B, nbatch, io, st);
+        if (!rc) e = cudaStreamSynchronize(st);
+        double sum[3] = {0.0, 0.0, 0.0};
+        for (int b = 0; !rc && e == cudaSuccess && b < nbatch; ++b) {
+            const int from[3] = {0, 1, 3}, to[3] = {1, 2, 4};
+            for (int i = 0; i < 3 && e == cudaSuccess; ++i) {
+                float t = 0.0f;
+                e = cudaEventElapsedTime(&t, ev[5 * b + from[i]], ev[5 * b + to[i]]);
+                sum[i] += t;
+            }
+        }
+        for (int i = 0; i < 3; ++i) ms[i] = (float)(sum[i] / nbatch);
+    }
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    if (rc) return rc;
+    if (e != cudaSuccess) return leg_set_error(LEG_ERR_CUDA, cudaGetErrorString(e));
+    return LEG_OK;
+}
 
 extern "C" int leg_forward_profiled(leg_plan_t p, const void *f, void *c, int B, cudaStream_t st, float *ms)
 {

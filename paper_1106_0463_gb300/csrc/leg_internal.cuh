@@ -182,6 +182,10 @@ struct LegPipeIO {
     void *stage[2] = {};
     cudaStream_t copy = nullptr;
     cudaEvent_t stage_ready[2] = {}, stage_free[2] = {};
+    // stage timing (or nullptr): five events per batch, recorded before and
+    // after its split and after its GEMM (GEMM stream), and before and after
+    // its transform (transform stream)
+    cudaEvent_t *prof = nullptr;
 };
 int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cudaStream_t st);
 bool leg_pipeline_applies(const leg_plan *p);

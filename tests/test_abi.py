@@ -63,6 +63,7 @@ def test_every_handle_entry_point_rejects_null_without_a_gpu(libpath):
         "leg_forward": ([vp, vp, vp, i, vp], (None, None, None, 4, None)),
         "leg_forward_profiled": ([vp, vp, vp, i, vp, vp], (None, None, None, 4, None, None)),
         "leg_forward_batches": ([vp, vp, vp, i, i, vp], (None, None, None, 4, 2, None)),
+        "leg_forward_batches_profiled": ([vp, vp, vp, i, i, vp, vp], (None, None, None, 4, 2, None, None)),
         "leg_backward": ([vp, vp, vp, i, vp], (None, None, None, 4, None)),
         "leg_plain_forward": ([vp, i, vp, i, vp, vp], (None, 0, None, 4, None, None)),
         "leg_plain_forward_cheb": ([vp, vp, i, i, vp, vp], (None, None, 8, 4, None, None)),

@@ -112,3 +112,16 @@ def test_host_batches_fp64_loop(leg):
     c = plan.forward_host_batches(fd.cpu().pin_memory())
     for b in range(nb):
         assert torch.equal(c[b], plan.forward(fd[b].contiguous()).cpu()), b
+
+
+def test_batches_profiled_equal_and_timed(leg):
+    """The profiled pipeline gives the same coefficients and positive stage
+    times (the GEMM longer than the split at this shape)."""
+    N, M, K, B, nb = 512, 2048, 1025, 256, 4
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    f = batches(nb, B, K, 31)
+    c = torch.empty((nb, B, N), device="cuda")
+    ms = plan.forward_batches_profiled(f, c)
+    assert all(t > 0 for t in ms) and ms[1] > ms[0], ms
+    for b in range(nb):
+        assert torch.equal(c[b], plan.forward(f[b].contiguous())), b
