@@ -537,20 +537,15 @@ int pipe_state(leg_plan *p, LegPipeState **out)
 // kernel is the one leg_forward launches for a batch of B.  With io.stage,
 // batch b's input is first copied from io.f (host) into staging buffer b % 2
 // on io.copy, after the split that last read that buffer.
-int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cudaStream_t st)
+namespace {
+// Queues the pipeline's launches on q's streams (and the copies on io.copy).
+int pipeline_body(leg_plan *p, LegPipeState *q, int B, int nbatch, const LegPipeIO &io)
 {
-    int rc = ensure_workspace(p, B);
-    if (rc) return rc;
-    LegPipeState *q = nullptr;
-    if ((rc = pipe_state(p, &q))) return rc;
+    int rc = LEG_OK;
     const LegSplitIn in = leg_split_workspace(p);
     float2 *Gs[2] = {static_cast<float2 *>(p->G), static_cast<float2 *>(p->Gbar)};
     const char *fb = static_cast<const char *>(io.f);
     char *cb = static_cast<char *>(io.c);
-    LEG_CUDA_TRY(cudaEventRecord(q->start, st));   // after the work already on `stream`
-    LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->start, 0));
-    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->start, 0));
-    if (io.stage[0]) LEG_CUDA_TRY(cudaStreamWaitEvent(io.copy, q->start, 0));
     for (int b = 0; b < nbatch; ++b) {
         const int s = b & 1;
         const float *fin = reinterpret_cast<const float *>(fb + io.fstride * b);
@@ -584,8 +579,29 @@ int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cuda
     if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (nbatch - 1) + 3], q->lo));
     if ((rc = leg_fft_forward(p, Gs[l], p->ldg, cb + io.cstride * (nbatch - 1), B, q->lo))) return rc;
     if (io.prof) LEG_CUDA_TRY(cudaEventRecord(io.prof[5 * (nbatch - 1) + 4], q->lo));
-    LEG_CUDA_TRY(cudaEventRecord(q->done, q->lo));
-    LEG_CUDA_TRY(cudaStreamWaitEvent(st, q->done, 0));   // later work on `stream` sees every batch
+    return LEG_OK;
+}
+}  // namespace
+
+int leg_pipeline_split(leg_plan *p, int B, int nbatch, const LegPipeIO &io, cudaStream_t st)
+{
+    int rc = ensure_workspace(p, B);
+    if (rc) return rc;
+    LegPipeState *q = nullptr;
+    if ((rc = pipe_state(p, &q))) return rc;
+    LEG_CUDA_TRY(cudaEventRecord(q->start, st));   // after the work already on `stream`
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->hi, q->start, 0));
+    LEG_CUDA_TRY(cudaStreamWaitEvent(q->lo, q->start, 0));
+    if (io.stage[0]) LEG_CUDA_TRY(cudaStreamWaitEvent(io.copy, q->start, 0));
+    rc = pipeline_body(p, q, B, nbatch, io);
+    // later work on `stream` follows everything queued, also after an error
+    // part of the way through
+    cudaError_t e = cudaEventRecord(q->gemm_done, q->hi);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, q->gemm_done, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(q->done, q->lo);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, q->done, 0);
+    if (rc) return rc;
+    if (e != cudaSuccess) return leg_set_error(LEG_ERR_CUDA, cudaGetErrorString(e));
     return LEG_OK;
 }
 
