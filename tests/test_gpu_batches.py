@@ -125,3 +125,37 @@ def test_batches_profiled_equal_and_timed(leg):
     assert all(t > 0 for t in ms) and ms[1] > ms[0], ms
     for b in range(nb):
         assert torch.equal(c[b], plan.forward(f[b].contiguous())), b
+
+
+def test_batches_inside_a_caller_capture(leg):
+    """On a stream being captured the batches run through leg_forward in
+    turn, so their launches join the caller's graph; a replay gives every
+    batch's coefficients."""
+    N, M, K, B, nb = 128, 512, 257, 60, 3
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    f = batches(nb, B, K, 51)
+    c = torch.empty((nb, B, N), device="cuda")
+    plan.reserve(B)
+    refs = [plan.forward(f[b].contiguous()).clone() for b in range(nb)]
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.forward_batches(f, c)
+    torch.cuda.current_stream().wait_stream(s)
+    c.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    for b in range(nb):
+        assert torch.equal(c[b], refs[b]), b
+    plan.status()
+
+
+def test_host_batches_single_batch(leg):
+    N, M, K, B = 128, 512, 257, 33
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    fd = batches(1, B, K, 61)
+    c = plan.forward_host_batches(fd.cpu().pin_memory())
+    assert torch.equal(c[0], plan.forward(fd[0].contiguous()).cpu())
