@@ -159,3 +159,13 @@ def test_host_batches_single_batch(leg):
     fd = batches(1, B, K, 61)
     c = plan.forward_host_batches(fd.cpu().pin_memory())
     assert torch.equal(c[0], plan.forward(fd[0].contiguous()).cpu())
+
+
+def test_batches_small_transform_length(leg):
+    """M = 128 (the shared-memory Stockham transform) through the pipeline."""
+    N, M, K = 32, 128, 65
+    plan = leg.Plan(N, M, K, 0, leg.SPLIT_FP16)
+    f = batches(5, 70, K, 71)
+    c = plan.forward_batches(f)
+    for b in range(5):
+        assert torch.equal(c[b], plan.forward(f[b].contiguous())), b
