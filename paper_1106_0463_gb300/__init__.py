@@ -170,6 +170,23 @@ def _host_tensor(t: torch.Tensor, dtype: torch.dtype, shape, name: str):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _batch_args(f, c, K: int, N: int, dtype: torch.dtype, check, suffix: str):
+    """Pointers and sizes of a stack of batches: f (nbatch, B, K) and c
+    (nbatch, B, N), both contiguous, checked by `check` (_dev_tensor or
+    _host_tensor) as (nbatch * B, K) and (nbatch * B, N) matrices."""
+    for t, name, w in ((f, "f" + suffix, K), (c, "c" + suffix, N)):
+        if not isinstance(t, torch.Tensor) or t.dim() != 3:
+            raise ValueError("%s must be a tensor of shape (nbatch, B, %d)" % (name, w))
+        if not t.is_contiguous():
+            raise ValueError("%s must be contiguous" % name)
+    nb, B = f.shape[0], f.shape[1]
+    if tuple(c.shape[:2]) != (nb, B):
+        raise ValueError("c%s must have shape (%d, %d, %d)" % (suffix, nb, B, N))
+    pf = check(f.view(nb * B, f.shape[2]), dtype, (nb * B, K), "f" + suffix)
+    pc = check(c.view(nb * B, c.shape[2]), dtype, (nb * B, N), "c" + suffix)
+    return pf, pc, nb, B
+
+
 class Plan:
     """An operator for one (N, M, K, Q, dtype); owns its device buffers.
 
@@ -284,16 +301,9 @@ class Plan:
         """leg_forward_batches: f of shape (nbatch, B, K) on the device, c of
         shape (nbatch, B, N); the batches one after another, pipelined for
         split-FP16 plans (each batch's transform beside the next one's GEMM)."""
-        if f.dim() != 3:
-            raise ValueError("f must have shape (nbatch, B, K)")
-        nb, B = f.shape[0], f.shape[1]
-        pf = _dev_tensor(f.view(nb * B, f.shape[2]) if f.is_contiguous() else f, self.io_dtype,
-                         (nb * B, self.K), "f")
-        if c is None:
-            c = torch.empty((nb, B, self.N), dtype=self.io_dtype, device=f.device)
-        if c.dim() != 3 or tuple(c.shape) != (nb, B, self.N):
-            raise ValueError("c must have shape (%d, %d, %d)" % (nb, B, self.N))
-        pc = _dev_tensor(c.view(nb * B, self.N) if c.is_contiguous() else c, self.io_dtype, (nb * B, self.N), "c")
+        if c is None and isinstance(f, torch.Tensor) and f.dim() == 3:
+            c = torch.empty((f.shape[0], f.shape[1], self.N), dtype=self.io_dtype, device=f.device)
+        pf, pc, nb, B = _batch_args(f, c, self.K, self.N, self.io_dtype, _dev_tensor, "")
         _check(_lib.leg_forward_batches(self._h, pf, pc, B, nb, _stream(stream)))
         return c
 
@@ -301,9 +311,7 @@ class Plan:
         """leg_forward_batches_profiled: the pipelined batches with the mean
         time per batch of each stage inside the pipeline; synchronises.
         Returns (prep_ms, gemm_ms, fft_ms)."""
-        nb, B = f.shape[0], f.shape[1]
-        pf = _dev_tensor(f.view(nb * B, -1), self.io_dtype, (nb * B, self.K), "f")
-        pc = _dev_tensor(c.view(nb * B, -1), self.io_dtype, (nb * B, self.N), "c")
+        pf, pc, nb, B = _batch_args(f, c, self.K, self.N, self.io_dtype, _dev_tensor, "")
         ms = (ctypes.c_float * 3)()
         _check(_lib.leg_forward_batches_profiled(self._h, pf, pc, B, nb, _stream(stream), ms))
         return tuple(float(v) for v in ms)
@@ -343,17 +351,9 @@ class Plan:
         N) on the CPU, ideally pinned (c_host pinned and allocated when None);
         pipelined for split-FP16 plans.  With sync=False the call returns at
         once and c_host is complete when the stream has reached it."""
-        if f_host.dim() != 3:
-            raise ValueError("f_host must have shape (nbatch, B, K)")
-        nb, B = f_host.shape[0], f_host.shape[1]
-        pf = _host_tensor(f_host.view(nb * B, -1) if f_host.is_contiguous() else f_host, self.io_dtype,
-                          (nb * B, self.K), "f_host")
-        if c_host is None:
-            c_host = torch.empty((nb, B, self.N), dtype=self.io_dtype).pin_memory()
-        if c_host.dim() != 3 or tuple(c_host.shape) != (nb, B, self.N):
-            raise ValueError("c_host must have shape (%d, %d, %d)" % (nb, B, self.N))
-        pc = _host_tensor(c_host.view(nb * B, self.N) if c_host.is_contiguous() else c_host, self.io_dtype,
-                          (nb * B, self.N), "c_host")
+        if c_host is None and isinstance(f_host, torch.Tensor) and f_host.dim() == 3:
+            c_host = torch.empty((f_host.shape[0], f_host.shape[1], self.N), dtype=self.io_dtype).pin_memory()
+        pf, pc, nb, B = _batch_args(f_host, c_host, self.K, self.N, self.io_dtype, _host_tensor, "_host")
         st = _stream(stream)
         _check(_lib.leg_forward_host_batches(self._h, pf, pc, B, nb, st))
         if sync:
