@@ -5,7 +5,7 @@ python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 One step = one forward pass of the sampled-input path over one batch with
 inputs resident in HBM: input split -> tcgen05 Abel GEMM -> transform with the
-(2n+1) scaling (leg_forward).  The headline workload is the largest dense
+(2n+1) scaling.  The headline workload is the largest dense
 single-GPU configuration: B=256 random decaying Chebyshev series at K=8193
 Chebyshev-Lobatto nodes, N=4096 coefficients, M=16384 trapezoid points (exact
 tau rule), on the split-FP16 path, its error against the FP64 oracle measured
@@ -22,11 +22,17 @@ the headline workload (FP64, FP32, BF16 next to split-FP16), the sine-form
 transform (Eq. 2.13) on the headline workload, and Table 1's |x|^{3/2} on
 the plain method at several (M, Q).
 
-Timing: W untimed warm-up steps; then, for each of K steps, L2 is flushed
-(a 512 MiB write) and the step is timed with CUDA events on the launch
-stream.  Barrier + synchronize bracket the timed steps; the max over ranks is
-taken.  Under torchrun (N > 1) every rank runs its own batch (weak scaling,
-no collective on the data path).
+Timing of the headline value: W untimed warm-up batches, then the K steps
+as K distinct batches (the workload's batch scaled per step, more bytes than
+L2 in all) in one leg_forward_batches call between a pair of CUDA events:
+each batch's split and GEMM on a high-priority stream, the previous batch's
+transform beside it on a low-priority one.  Barrier + synchronize bracket the
+timed region; the max over ranks is taken.  The same workload one batch per
+step (L2 flushed by a 512 MiB write before each, CUDA events on the launch
+stream) gives the single_batch figures, stage times and error; the other
+workloads are timed that way too.  e2e runs the K batches from pinned host
+memory through leg_forward_host_batches.  Under torchrun (N > 1) every rank
+runs its own batches (weak scaling, no collective on the data path).
 
 --impl reference times the FP64 CPU oracle on the host cores, on a bounded
 sample of the same workload per step.
